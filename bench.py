@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 DG Euler solver in DOF-updates per second per RK stage.
+
+One bench step = one full pass of the hot path on the resident state:
+the CFL time-step reduction, one five-stage LSERK45 step (per stage: the
+interface-flux kernel and the fused volume/lift/update kernel) and the
+quadrature integrals of the new state.  value = DOF x 5 stages x steps x ranks
+/ max-over-ranks time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Multi-GPU: one process per GPU (torchrun), each rank an independent replica
+of the workload (the path has no data exchange on one box): weak scaling.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TWO_PI = 2 * math.pi
+WORKLOADS = {
+    # the headline: inviscid Taylor-Green vortex, Mach 0.1, 64^3 elements, p = 4, FP64
+    "tgv64_p4_fp64": dict(nel=(64, 64, 64), p=4, box=(0, 0, 0, TWO_PI, TWO_PI, TWO_PI),
+                          init="tgv", params=[1.0, 1.0, 0.1], prec="fp64", cfl=0.5,
+                          desc="inviscid Taylor-Green vortex, Mach 0.1, periodic [0,2pi]^3, "
+                               "64^3 hex elements, p=4 (125 nodes/element), FP64 state"),
+    # FP32 bulk form: isentropic vortex, 128^3 elements, p = 3
+    "vortex128_p3_fp32": dict(nel=(128, 128, 128), p=3, box=(0, 0, 0, 16.0, 16.0, 16.0),
+                              init="vortex", params=None, prec="fp32", cfl=0.5,
+                              desc="isentropic vortex (seed 0) on a periodic 16^3 box, 128^3 hex "
+                                   "elements, p=3, FP32 state and arithmetic, FP64 reductions"),
+    # small cases (profiling captures, quick checks)
+    "tgv32_p4_fp64": dict(nel=(32, 32, 32), p=4, box=(0, 0, 0, TWO_PI, TWO_PI, TWO_PI),
+                          init="tgv", params=[1.0, 1.0, 0.1], prec="fp64", cfl=0.5,
+                          desc="Taylor-Green vortex, 32^3 elements, p=4, FP64"),
+    "vortex8_p3_fp64": dict(nel=(8, 8, 8), p=3, box=(0, 0, 0, 10.0, 10.0, 10.0),
+                            init="vortex", params=None, prec="fp64", cfl=0.5,
+                            desc="isentropic vortex (seed 0), [0,10]^3, 8^3 elements, p=3, FP64"),
+}
+DEFAULT = "tgv64_p4_fp64"
+METRIC = "DOF-updates/s per RK stage"
+UNIT = "DOF-stage/s"
+
+# FP64 peak of the GB300 CUDA cores, derived from unit counts and clock: NVIDIA's
+# nominal 1.25 TFLOP/s FP64 at the 2070 MHz maximum SM clock is 4 flop per SM
+# per clock (2 FP64 FMA lanes per SM) x 152 SMs.
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.070e9 / 1e12  # 128 FP32 FMA lanes/SM at max clock
+
+
+def kernel_flops(kind, N, E):
+    """Algorithmic flops per launch of the kernels (FMA = 2, div = sqrt = 1),
+    counted from the arithmetic they execute ("Kernels")."""
+    if kind == "volume":  # flux 28 + contraction 30N + lift 60 + RK update 25, per node
+        return E * N ** 3 * (113 + 30 * N)
+    if kind == "face":  # traces 20N + Lax-Friedrichs 69, per unique face point
+        return 3 * E * N ** 2 * (69 + 20 * N)
+    return 0
+
+
+def kernel_bytes(kind, N, E, esz):
+    """Algorithmic HBM bytes per launch (each array element read or written once)."""
+    nodes = E * N ** 3
+    fpts = 3 * E * N ** 2
+    if kind == "volume":  # Q, dQ read; Q, dQ written; interface fluxes read
+        return nodes * 5 * esz * 4 + fpts * 5 * esz
+    if kind == "face":  # Q read; interface fluxes written
+        return nodes * 5 * esz + fpts * 5 * esz
+    if kind == "cfl":
+        return nodes * 5 * esz
+    if kind == "norms":
+        return nodes * 5 * esz
+    return 0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv") \
+            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/dg_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("dg_kernels.cuh",):
+        with open(os.path.join(ROOT, "paper_2006_15698_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(workload, kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    ent = d.get(workload, {}).get(kernel)
+    if not ent or ent.get("kernel_source_sha") != _kernel_hash():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_rate(w, nel, steps):
+    """DOF-stage/s of the FP64 CPU oracle on `steps` LSERK45 steps of workload w
+    on an nel box (CFL reduction + steps + integrals); returns (rate, cores, seconds)."""
+    import oracle
+    nx, ny, nz = nel
+    box = w["box"]
+    # keep the element size of the workload: shrink the box with the element count
+    sx, sy, sz = (nel[i] / w["nel"][i] for i in range(3))
+    b = (box[0], box[1], box[2], box[3] * sx, box[4] * sy, box[5] * sz)
+    om = oracle.Mesh(nx, ny, nz, w["p"], *b)
+    Q = om.init(w["init"], _params(w))
+    cores = oracle.num_threads()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        dt, _ = om.cfl_dt(Q, w["cfl"])
+        Q, _ = om.rk_steps(Q, dt, 1)
+        om.norms(Q)
+    sec = time.perf_counter() - t0
+    dof = nx * ny * nz * (w["p"] + 1) ** 3
+    return dof * 5 * steps / sec, cores, sec
+
+
+def _params(w):
+    if w["params"] is not None:
+        return w["params"]
+    from paper_2006_15698_gb300 import inputs
+    return inputs.vortex_params(0, w["box"])
+
+
+def run_reference(args, w):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    # each step: one LSERK45 step of a 16^3-element box of the same problem
+    # (same element size, order and physics; the oracle's cost per DOF does
+    # not depend on the element count)
+    nel = tuple(min(16, n) for n in w["nel"])
+    for _ in range(args.warmup):
+        oracle_rate(w, nel, 1)
+    rate, cores, sec = oracle_rate(w, nel, args.steps)
+    dof = nel[0] * nel[1] * nel[2] * (w["p"] + 1) ** 3
+    out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": _config(w, args.workload),
+           "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{args.steps} LSERK45 steps (CFL + 5 stages + integrals) of "
+                                      f"the same problem on a {nel[0]}x{nel[1]}x{nel[2]}-element "
+                                      f"box ({dof} DOF), plain FP64 C oracle, OpenMP over elements"},
+           "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def _config(w, name):
+    nx, ny, nz = w["nel"]
+    N = w["p"] + 1
+    return {"workload": f"{name}: {w['desc']}; one step = CFL reduction + LSERK45 step + integrals",
+            "elements": nx * ny * nz, "p": w["p"], "dof": nx * ny * nz * N ** 3,
+            "unknowns": 5 * nx * ny * nz * N ** 3, "cfl": w["cfl"], "precision": w["prec"]}
+
+
+# ----------------------------------------------------------------------------
+# GPU run
+# ----------------------------------------------------------------------------
+
+def run_native(args, w):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    from paper_2006_15698_gb300 import dg
+
+    nx, ny, nz = w["nel"]
+    N = w["p"] + 1
+    E = nx * ny * nz
+    prec = dg.DG_FP64 if w["prec"] == "fp64" else dg.DG_FP32
+    esz = 8 if prec == dg.DG_FP64 else 4
+    m = dg.Mesh(nx, ny, nz, w["p"], *w["box"], precision=prec)
+    stream = torch.cuda.current_stream()
+    Q = m.init(w["init"], _params(w))
+    dQ = torch.zeros_like(Q)
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    integ = torch.zeros(dg.DG_NORMS_LEN, dtype=torch.float64, device="cuda")
+
+    def step():
+        m.cfl_dt(Q, w["cfl"], dt)
+        m.rk_step(Q, dQ, dt)
+        m.norms(Q, out=integ)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.25)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    m.profile_begin()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = m.profile_end()
+    if ws > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    ck = clocks.stop()
+    err = m.last_error()
+
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    dof = E * N ** 3
+    value = dof * 5 * args.steps * ws / (ms_max / 1e3)
+
+    # ---- end-to-end through host buffers: H2D state, step, D2H state + integrals
+    e2e_steps = max(1, min(args.steps, 10))
+    Qh = torch.empty(Q.shape, dtype=Q.dtype, pin_memory=True)
+    Qh.copy_(Q)
+    integ_h = torch.empty(dg.DG_NORMS_LEN, dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        Q.copy_(Qh, non_blocking=True)
+        step()
+        Qh.copy_(Q, non_blocking=True)
+        integ_h.copy_(integ, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
+    e2e_val = dof * 5 * e2e_steps * ws / (float(e2e_ms.item()) / 1e3)
+
+    out = None
+    if rank == 0:
+        peaks, src = _peaks()
+        kernels = {k: {"ms_total": v[0], "launches": v[1],
+                       "ms_per_launch": (v[0] / v[1] if v[1] else None)}
+                   for k, v in prof.items() if v[1]}
+        dom = max(("face", "volume"), key=lambda k: prof[k][0])
+        avg_s = prof[dom][0] / prof[dom][1] / 1e3
+        if prec == dg.DG_FP64:
+            ach = kernel_flops(dom, N, E) / avg_s / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS,
+                    "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                    "kernel": dom}
+        else:
+            gbs = kernel_bytes(dom, N, E, esz) / avg_s / 1e9
+            roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": gbs / peaks["hbm_gbs"], "peak_source": src, "kernel": dom}
+        roof["traffic"] = _traffic(args.workload, dom)
+        # HBM view of the whole step for context: algorithmic state traffic per stage
+        hbm_step = (prof["face"][0] + prof["volume"][0]) / 1e3 / (prof["volume"][1] or 1)
+        hbm_bytes = sum(kernel_bytes(k, N, E, esz) for k in ("face", "volume"))
+        roof["stage_hbm_gbs_algorithmic"] = hbm_bytes / hbm_step / 1e9
+        roof["stage_hbm_frac_of_measured"] = roof["stage_hbm_gbs_algorithmic"] / peaks["hbm_gbs"]
+        launches = (prof["face"][1] + prof["volume"][1] + 2 * prof["cfl"][1] + 2 * prof["norms"][1])
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64" if prec == dg.DG_FP64 else "f32",
+               "data": "synthetic",
+               "config": dict(_config(w, args.workload), parallelism=f"replicas x{ws}",
+                              l2=f"state arrays {m.state_bytes / 1e9:.2f} GB each, larger than the 129 MB L2"),
+               "roofline": roof, "gpu_launches": launches, "kernels": kernels,
+               "e2e": {"value": e2e_val, "unit": UNIT, "steps": e2e_steps,
+                       "h2d_bytes_per_step": m.state_bytes,
+                       "d2h_bytes_per_step": m.state_bytes + 8 * dg.DG_NORMS_LEN},
+               "clocks": ck, "device_error_flag": err}
+    if ws > 1:
+        dist.barrier()
+    del m
+    torch.cuda.synchronize()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    ws, rank, _ = _dist()
+    out = run_native(args, w)
+    if rank == 0 and out is not None:
+        if ws == 1 and not args.no_cpu_baseline:
+            # bounded sample: one LSERK45 step of the full workload if it is
+            # small enough for the host, else of a box with the same element size
+            dof_full = out["config"]["dof"]
+            nel = w["nel"] if dof_full <= 40_000_000 else tuple(min(32, n) for n in w["nel"])
+            rate, cores, sec = oracle_rate(w, nel, 1)
+            out["cpu_baseline"] = {
+                "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"1 LSERK45 step (CFL + 5 stages + integrals) of the workload on "
+                          f"{nel[0]}x{nel[1]}x{nel[2]} elements, {sec:.1f} s, plain FP64 C oracle"}
+        print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * dg.h -- C ABI of the GB300 (sm_103a) discontinuous Galerkin Euler library.
+ *
+ * The library evaluates the collocated Gauss-Legendre DG right-hand side of
+ * the 3D compressible Euler equations on periodic Cartesian hexahedral meshes
+ * and advances it with the five-stage low-storage Runge-Kutta scheme, after
+ * Kirby & Mavriplis, "GPU-Accelerated Discontinuous Galerkin Methods: 30x
+ * Speedup on 345 Billion Unknowns" (arXiv 2006.15698):
+ *   governing equations and flux ........................ Sec. II.A, Eq. 1-2
+ *   ideal-gas closure, gamma ............................. Sec. II.A, Eq. 3
+ *   weak form integrated by parts ........................ Sec. II.B, Eq. 4-5
+ *   Lax-Friedrichs interface flux ........................ Sec. II.B
+ *   nodal Lagrange basis on N = p+1 Gauss-Legendre points  Sec. II.B, Eq. 6-7
+ *   low-storage explicit RK time integration ............. Sec. II.B, Sec. IV, Sec. VI.A
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * State arrays.  A state holds the conservative variables
+ * (rho, rho u, rho v, rho w, rho E) at every node of every element, as
+ *     Q[field][element][k][j][i]     (C order, i fastest)
+ * with element index e = ex + nx*(ey + ny*ez) and node (i,j,k) at the
+ * Gauss-Legendre points xi_i, xi_j, xi_k of the reference cube [-1,1]^3, i.e.
+ * at x = x0 + (ex + (xi_i + 1)/2) hx, hx = Lx/nx (likewise y, z).  The scalar
+ * type is double for DG_FP64 meshes and float for DG_FP32 meshes;
+ * dg_mesh_sizes gives the byte size.  State arrays are DEVICE memory owned by
+ * the caller (for instance torch tensors); the library never allocates,
+ * frees or retains them, and reads/writes them only inside the calls.
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream).  Every call except dg_mesh_create/destroy/sizes,
+ * dg_status_string and dg_last_error is asynchronous on that stream: it
+ * validates its arguments on the host, enqueues kernels and returns.  Calls
+ * on one mesh handle share the handle's workspace, so they must be ordered
+ * (one stream, or explicit events); concurrent calls on one handle race.
+ *
+ * Errors.  Arguments are checked on the host before anything is enqueued
+ * (DG_ERR_ARG, DG_ERR_UNSUPPORTED).  A CUDA launch or allocation failure is
+ * DG_ERR_CUDA / DG_ERR_OOM.  Kernels never trap: a non-positive or non-finite
+ * density or pressure seen by dg_cfl_dt sets a sticky device flag that
+ * dg_last_error reports (DG_ERR_NONFINITE) and the time step it writes is NaN.
+ *
+ * Device.  A mesh handle belongs to the device that was current when it was
+ * created; calls must be made with that device current.
+ */
+#ifndef DG_GB300_H
+#define DG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DG_OK = 0,
+    DG_ERR_ARG = 1,         /* a NULL pointer, non-positive size, bad enum value */
+    DG_ERR_UNSUPPORTED = 2, /* p outside [0, DG_MAX_P] */
+    DG_ERR_OOM = 3,         /* device allocation of the handle's workspace failed */
+    DG_ERR_CUDA = 4,        /* a CUDA call or kernel launch failed */
+    DG_ERR_NONFINITE = 5,   /* a kernel met rho <= 0, p <= 0 or a NaN (device flag) */
+    DG_ERR_BOUNDS = 6,      /* reserved: an index check in a checking build failed */
+    DG_ERR_TIMEOUT = 7      /* reserved: a bounded wait ran out */
+} dg_status;
+
+typedef enum {
+    DG_FP64 = 0, /* double state, double arithmetic */
+    DG_FP32 = 1  /* float state and volume/surface arithmetic; double reductions
+                    (time step, integrals, norms) */
+} dg_precision;
+
+typedef enum {
+    DG_INIT_UNIFORM = 0, /* params {rho, u, v, w, p} */
+    DG_INIT_VORTEX = 1,  /* params {beta, xc, yc, u_inf, v_inf, w_inf, t} */
+    DG_INIT_TGV = 2      /* params {rho0, V0, Mach} */
+} dg_init_kind;
+
+#define DG_MAX_P 6
+#define DG_NORMS_LEN 7
+
+typedef struct dg_mesh dg_mesh;
+
+/* Create a handle for a periodic box [x0, x0+Lx] x [y0, y0+Ly] x [z0, z0+Lz]
+ * split into nx*ny*nz equal hexahedral elements of polynomial degree p
+ * (N = p+1 Gauss-Legendre nodes per direction, Sec. II.B, Eq. 7), ratio of
+ * specific heats gamma (Eq. 3).  The handle computes the 1D operators of the
+ * collocated basis on the host (nodes, weights, weak derivative, face
+ * interpolation and lift vectors) and allocates its device workspace on the
+ * current device: the interface-flux buffer (3 faces x N^2 points x 5 fields
+ * per element, in the mesh's scalar type), the reduction partials and the
+ * error flag.  Sizes: 1 <= nx, ny, nz; nx*ny*nz*N^3 < 2^40; 0 <= p <= 6;
+ * L > 0; gamma > 1.  On success *out owns the handle (free with
+ * dg_mesh_destroy).  Errors: DG_ERR_ARG, DG_ERR_UNSUPPORTED, DG_ERR_OOM,
+ * DG_ERR_CUDA; *out is set to NULL on error. */
+dg_status dg_mesh_create(int nx, int ny, int nz, int p,
+                         double x0, double y0, double z0,
+                         double Lx, double Ly, double Lz,
+                         double gamma, dg_precision precision, dg_mesh **out);
+
+/* Free the handle and its device workspace (synchronises the device first).
+ * NULL is ignored. */
+void dg_mesh_destroy(dg_mesh *mesh);
+
+/* Sizes of the mesh: n_dof = elements * N^3 nodes, n_unknowns = 5 * n_dof
+ * (Sec. V-VI count both), state_bytes = bytes of one state array,
+ * workspace_bytes = device bytes the handle holds.  Any output may be NULL. */
+dg_status dg_mesh_sizes(const dg_mesh *mesh, int64_t *n_dof, int64_t *n_unknowns,
+                        size_t *state_bytes, size_t *workspace_bytes);
+
+/* Fill the device state Q with an initial condition evaluated at the nodes
+ * (kinds and parameters above; the vortex is the isentropic vortex carried by
+ * (u_inf, v_inf, w_inf) to time t, columnar along z, with minimum-image
+ * distances on the periodic box; TGV is the Taylor-Green vortex with
+ * p0 = rho0 V0^2 / (gamma Mach^2)).  params is a HOST array of nparams
+ * doubles.  Errors: DG_ERR_ARG (unknown kind, too few params, NULL). */
+dg_status dg_state_init(const dg_mesh *mesh, dg_init_kind kind, const double *params,
+                        int nparams, void *Q, void *stream);
+
+/* Semi-discrete right-hand side dQ/dt = M^{-1} R(Q) of Eq. 5 with collocated
+ * quadrature: the volume term (sum-factorised weak derivative of the Euler
+ * fluxes, Eq. 2), minus the lifted local Lax-Friedrichs interface fluxes of
+ * the six faces, divided by the diagonal mass matrix.  Q and R are device
+ * states of this mesh; R must not overlap Q.  Uses the handle's interface-
+ * flux buffer. */
+dg_status dg_rhs(const dg_mesh *mesh, const void *Q, void *R, void *stream);
+
+/* Stable time step for the current state (the paper states no rule; this
+ * library uses dt = cfl * min(hx, hy, hz) / ((2p+1) * Lambda) with
+ * Lambda = max over nodes of sum_d (|u_d| + c), c = sqrt(gamma p / rho),
+ * reduced in double precision).  Writes dt to the DEVICE double *dt_dev,
+ * with no host synchronisation.  A node with rho <= 0, p <= 0 or NaN makes
+ * dt NaN and sets the DG_ERR_NONFINITE flag.  Errors: DG_ERR_ARG (cfl <= 0). */
+dg_status dg_cfl_dt(const dg_mesh *mesh, const void *Q, double cfl, double *dt_dev,
+                    void *stream);
+
+/* One step of the five-stage fourth-order 2N-storage Runge-Kutta scheme
+ * (Carpenter & Kennedy 1994; Sec. VI.A "LSERK45") with the time step read
+ * from the DEVICE double *dt_dev:  for s = 1..5:
+ *     dQ <- A_s dQ + dt * dQ/dt(Q),   Q <- Q + B_s dQ      (A_1 = 0)
+ * Q is updated in place; dQ is a device state-sized register whose incoming
+ * contents are ignored (it holds the last stage's increment on return).
+ * Each stage evaluates the right-hand side of the whole mesh at the
+ * stage-start state.  Uses the handle's interface-flux buffer. */
+dg_status dg_rk_step(const dg_mesh *mesh, void *Q, void *dQ, const double *dt_dev,
+                     void *stream);
+
+/* Quadrature integrals of the state with the collocated rule (weight
+ * J w_i w_j w_k per node, J = hx hy hz / 8), accumulated in double in a fixed
+ * order (the result is bitwise reproducible for a given mesh):
+ *   out[0..4] = integral of each conserved field,
+ *   out[5]    = integral of the kinetic energy |rho u|^2 / (2 rho),
+ *   out[6]    = ||Q - Qref|| / ||Qref|| (L2 over the five fields), 0 if Qref is NULL.
+ * out is a DEVICE array of DG_NORMS_LEN doubles, written asynchronously. */
+dg_status dg_norms(const dg_mesh *mesh, const void *Q, const void *Qref, double *out,
+                   void *stream);
+
+/* Per-kernel timing, the library's counterpart of the per-kernel breakdown
+ * the paper reports (Sec. VI.B, Table II: Volume, Surface, Update-Project).
+ * Between dg_profile_begin and dg_profile_end every kernel launch made for
+ * this mesh is bracketed by two CUDA events recorded on its launching stream.
+ * dg_profile_end synchronises on the last event, and writes, per kernel kind
+ * (array index), the summed device time in milliseconds and the number of
+ * launches:
+ *   DG_KERNEL_FACE   interface traces + Lax-Friedrichs fluxes
+ *   DG_KERNEL_VOLUME volume flux derivative + lift + (RK update or rhs write)
+ *   DG_KERNEL_CFL    time-step reduction (two launches counted as one)
+ *   DG_KERNEL_NORMS  integrals (two launches counted as one)
+ *   DG_KERNEL_INIT   initial state
+ * ms and launches are HOST arrays of DG_PROFILE_KINDS entries.  Recording
+ * costs one event pair per launch; begin discards earlier records. */
+#define DG_PROFILE_KINDS 5
+enum { DG_KERNEL_FACE = 0, DG_KERNEL_VOLUME = 1, DG_KERNEL_CFL = 2, DG_KERNEL_NORMS = 3,
+       DG_KERNEL_INIT = 4 };
+dg_status dg_profile_begin(dg_mesh *mesh);
+dg_status dg_profile_end(dg_mesh *mesh, double *ms, int64_t *launches);
+
+/* Static text for a status code. */
+const char *dg_status_string(dg_status status);
+
+/* Read and clear the handle's sticky device error flag (synchronises the
+ * device).  DG_OK if no kernel raised it since the last read. */
+dg_status dg_last_error(const dg_mesh *mesh);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_GB300_H */

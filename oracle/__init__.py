@@ -56,6 +56,8 @@ def _bind(lib):
     lib.dgo_lf_flux.restype = None
     lib.dgo_rhs_o1.argtypes = [M, _DP, _DP]
     lib.dgo_rhs_o2.argtypes = [M, _DP, _DP]
+    lib.dgo_rhs_o2_elements.argtypes = [M, _DP, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_int64), _DP]
     lib.dgo_lserk_coeffs.argtypes = [_DP, _DP]
     lib.dgo_lserk_coeffs.restype = None
     lib.dgo_lserk_ode.argtypes = [ctypes.c_int64, _DP, ctypes.c_int, ctypes.c_double, _ODE_CB]
@@ -107,6 +109,17 @@ class Mesh:
         st = fn(ctypes.byref(self._m), _ptr(Q), _ptr(R))
         if st:
             raise RuntimeError(f"oracle rhs failed ({st})")
+        return R
+
+    def rhs_elements(self, Q, elems):
+        """O2 right-hand side of the listed elements only: shape (5, len(elems), N, N, N)."""
+        Q = _f64(Q)
+        el = np.ascontiguousarray(np.asarray(elems, dtype=np.int64))
+        R = np.empty((NF, el.size, self.N, self.N, self.N))
+        st = self.lib.dgo_rhs_o2_elements(ctypes.byref(self._m), _ptr(Q), el.size,
+                                          el.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(R))
+        if st:
+            raise RuntimeError(f"oracle rhs_elements failed ({st})")
         return R
 
     def rk_steps(self, Q, dt, nsteps=1):

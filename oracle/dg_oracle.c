@@ -268,86 +268,134 @@ static void collocated_trace(const dgo_mesh *m, const basis1d *b, const double *
  * (normal +x: the element is the left state, its +x neighbour the right) and
  * F*x(-face) the flux through its -x face (left state: the -x neighbour).
  * The outward normal on the -x face is -x, hence the sign of that term. */
-int dgo_rhs_o2(const dgo_mesh *m, const double *Q, double *R)
+/* O2 for one element e: out[n * N^3 + node] = R of field n at node (i,j,k). */
+static void rhs_o2_element(const dgo_mesh *m, const basis1d *bp, const double *Q, int64_t e,
+                           double *out)
 {
-    if (!mesh_ok(m) || !Q || !R) return 1;
+    const basis1d b = *bp;
     const int N = m->p + 1;
-    basis1d b;
-    make_basis(N, &b);
+    const int N3 = N * N * N;
     const double h[3] = {m->Lx / m->nx, m->Ly / m->ny, m->Lz / m->nz};
     const double J = h[0] * h[1] * h[2] / 8.0;
     const double sJ[3] = {h[1] * h[2] / 4.0, h[0] * h[2] / 4.0, h[0] * h[1] / 4.0};
     const double gam = m->gamma;
-    const int64_t E = n_elem(m);
+    int ex = (int)(e % m->nx);
+    int ey = (int)((e / m->nx) % m->ny);
+    int ez = (int)(e / ((int64_t)m->nx * m->ny));
+    double fx[NMAX * NMAX * NMAX][NF], fy[NMAX * NMAX * NMAX][NF], fz[NMAX * NMAX * NMAX][NF];
+    /* fluxes at every node */
+    for (int k = 0; k < N; ++k)
+        for (int j = 0; j < N; ++j)
+            for (int i = 0; i < N; ++i) {
+                double q[NF];
+                load_node(m, Q, e, i, j, k, q);
+                int id = (k * N + j) * N + i;
+                dgo_flux(0, q, gam, fx[id]);
+                dgo_flux(1, q, gam, fy[id]);
+                dgo_flux(2, q, gam, fz[id]);
+            }
+    /* interface fluxes on the six faces, fhat[d][side][t2*N+t1][n],
+     * side 0 = -face, side 1 = +face */
+    double fhat[3][2][NMAX * NMAX][NF];
+    for (int d = 0; d < 3; ++d) {
+        int64_t em = neighbour(m, ex, ey, ez, d, -1);
+        int64_t ep = neighbour(m, ex, ey, ez, d, +1);
+        for (int t2 = 0; t2 < N; ++t2)
+            for (int t1 = 0; t1 < N; ++t1) {
+                double qL[NF], qR[NF];
+                /* -face: left = -neighbour at its +1 end, right = this at -1 */
+                collocated_trace(m, &b, Q, em, d, +1, t1, t2, qL);
+                collocated_trace(m, &b, Q, e, d, -1, t1, t2, qR);
+                dgo_lf_flux(d, qL, qR, gam, fhat[d][0][t2 * N + t1]);
+                /* +face: left = this at +1, right = +neighbour at -1 */
+                collocated_trace(m, &b, Q, e, d, +1, t1, t2, qL);
+                collocated_trace(m, &b, Q, ep, d, -1, t1, t2, qR);
+                dgo_lf_flux(d, qL, qR, gam, fhat[d][1][t2 * N + t1]);
+            }
+    }
+    for (int k = 0; k < N; ++k)
+        for (int j = 0; j < N; ++j)
+            for (int i = 0; i < N; ++i) {
+                for (int n = 0; n < NF; ++n) {
+                    double vol = 0.0;
+                    for (int a = 0; a < N; ++a)
+                        vol += J * b.w[a] * b.w[j] * b.w[k] * (2.0 / h[0]) *
+                               b.dl[i][a] * fx[(k * N + j) * N + a][n];
+                    for (int bb = 0; bb < N; ++bb)
+                        vol += J * b.w[i] * b.w[bb] * b.w[k] * (2.0 / h[1]) *
+                               b.dl[j][bb] * fy[(k * N + bb) * N + i][n];
+                    for (int c = 0; c < N; ++c)
+                        vol += J * b.w[i] * b.w[j] * b.w[c] * (2.0 / h[2]) *
+                               b.dl[k][c] * fz[(c * N + j) * N + i][n];
+                    double surf = 0.0;
+                    /* x faces: face node (t1,t2) = (j,k) */
+                    surf += sJ[0] * b.w[j] * b.w[k] *
+                            (b.lp[i] * fhat[0][1][k * N + j][n] -
+                             b.lm[i] * fhat[0][0][k * N + j][n]);
+                    /* y faces: face node (t1,t2) = (i,k) */
+                    surf += sJ[1] * b.w[i] * b.w[k] *
+                            (b.lp[j] * fhat[1][1][k * N + i][n] -
+                             b.lm[j] * fhat[1][0][k * N + i][n]);
+                    /* z faces: face node (t1,t2) = (i,j) */
+                    surf += sJ[2] * b.w[i] * b.w[j] *
+                            (b.lp[k] * fhat[2][1][j * N + i][n] -
+                             b.lm[k] * fhat[2][0][j * N + i][n]);
+                    double mass = J * b.w[i] * b.w[j] * b.w[k];
+                    out[n * N3 + (k * N + j) * N + i] = (vol - surf) / mass;
+                }
+            }
+}
 
+/* R = dQ/dt = M^{-1} (volume term - surface term), in the layout above.
+ * For element e, node (i,j,k), field n, with J = hx hy hz / 8 and the x-faces'
+ * surface Jacobian hy hz / 4 (and likewise for y, z):
+ *   vol  = sum_a J w_a w_j w_k (2/hx) l_i'(xi_a) F^x_n(Q_ajk)
+ *        + sum_b J w_i w_b w_k (2/hy) l_j'(xi_b) F^y_n(Q_ibk)
+ *        + sum_c J w_i w_j w_c (2/hz) l_k'(xi_c) F^z_n(Q_ijc)
+ *   surf = (hy hz/4) w_j w_k [ l_i(+1) F*x(+face)_jk - l_i(-1) F*x(-face)_jk ]
+ *        + (same for y, z)
+ *   R    = (vol - surf) / (J w_i w_j w_k)
+ * where F*x(+face) is the Lax-Friedrichs flux through the element's +x face
+ * (normal +x: the element is the left state, its +x neighbour the right) and
+ * F*x(-face) the flux through its -x face (left state: the -x neighbour).
+ * The outward normal on the -x face is -x, hence the sign of that term. */
+int dgo_rhs_o2(const dgo_mesh *m, const double *Q, double *R)
+{
+    if (!mesh_ok(m) || !Q || !R) return 1;
+    const int N = m->p + 1;
+    const int N3 = N * N * N;
+    basis1d b;
+    make_basis(N, &b);
+    const int64_t E = n_elem(m);
 #pragma omp parallel for schedule(static)
     for (int64_t e = 0; e < E; ++e) {
-        int ex = (int)(e % m->nx);
-        int ey = (int)((e / m->nx) % m->ny);
-        int ez = (int)(e / ((int64_t)m->nx * m->ny));
-        double fx[NMAX * NMAX * NMAX][NF], fy[NMAX * NMAX * NMAX][NF],
-            fz[NMAX * NMAX * NMAX][NF];
-        /* fluxes at every node */
-        for (int k = 0; k < N; ++k)
-            for (int j = 0; j < N; ++j)
-                for (int i = 0; i < N; ++i) {
-                    double q[NF];
-                    load_node(m, Q, e, i, j, k, q);
-                    int id = (k * N + j) * N + i;
-                    dgo_flux(0, q, gam, fx[id]);
-                    dgo_flux(1, q, gam, fy[id]);
-                    dgo_flux(2, q, gam, fz[id]);
-                }
-        /* interface fluxes on the six faces, fhat[d][side][t2*N+t1][n],
-         * side 0 = -face, side 1 = +face */
-        double fhat[3][2][NMAX * NMAX][NF];
-        for (int d = 0; d < 3; ++d) {
-            int64_t em = neighbour(m, ex, ey, ez, d, -1);
-            int64_t ep = neighbour(m, ex, ey, ez, d, +1);
-            for (int t2 = 0; t2 < N; ++t2)
-                for (int t1 = 0; t1 < N; ++t1) {
-                    double qL[NF], qR[NF];
-                    /* -face: left = -neighbour at its +1 end, right = this at -1 */
-                    collocated_trace(m, &b, Q, em, d, +1, t1, t2, qL);
-                    collocated_trace(m, &b, Q, e, d, -1, t1, t2, qR);
-                    dgo_lf_flux(d, qL, qR, gam, fhat[d][0][t2 * N + t1]);
-                    /* +face: left = this at +1, right = +neighbour at -1 */
-                    collocated_trace(m, &b, Q, e, d, +1, t1, t2, qL);
-                    collocated_trace(m, &b, Q, ep, d, -1, t1, t2, qR);
-                    dgo_lf_flux(d, qL, qR, gam, fhat[d][1][t2 * N + t1]);
-                }
-        }
-        for (int k = 0; k < N; ++k)
-            for (int j = 0; j < N; ++j)
-                for (int i = 0; i < N; ++i) {
-                    for (int n = 0; n < NF; ++n) {
-                        double vol = 0.0;
-                        for (int a = 0; a < N; ++a)
-                            vol += J * b.w[a] * b.w[j] * b.w[k] * (2.0 / h[0]) *
-                                   b.dl[i][a] * fx[(k * N + j) * N + a][n];
-                        for (int bb = 0; bb < N; ++bb)
-                            vol += J * b.w[i] * b.w[bb] * b.w[k] * (2.0 / h[1]) *
-                                   b.dl[j][bb] * fy[(k * N + bb) * N + i][n];
-                        for (int c = 0; c < N; ++c)
-                            vol += J * b.w[i] * b.w[j] * b.w[c] * (2.0 / h[2]) *
-                                   b.dl[k][c] * fz[(c * N + j) * N + i][n];
-                        double surf = 0.0;
-                        /* x faces: face node (t1,t2) = (j,k) */
-                        surf += sJ[0] * b.w[j] * b.w[k] *
-                                (b.lp[i] * fhat[0][1][k * N + j][n] -
-                                 b.lm[i] * fhat[0][0][k * N + j][n]);
-                        /* y faces: face node (t1,t2) = (i,k) */
-                        surf += sJ[1] * b.w[i] * b.w[k] *
-                                (b.lp[j] * fhat[1][1][k * N + i][n] -
-                                 b.lm[j] * fhat[1][0][k * N + i][n]);
-                        /* z faces: face node (t1,t2) = (i,j) */
-                        surf += sJ[2] * b.w[i] * b.w[j] *
-                                (b.lp[k] * fhat[2][1][j * N + i][n] -
-                                 b.lm[k] * fhat[2][0][j * N + i][n]);
-                        double mass = J * b.w[i] * b.w[j] * b.w[k];
-                        R[qidx(m, n, e, i, j, k)] = (vol - surf) / mass;
-                    }
-                }
+        double out[NF * NMAX * NMAX * NMAX];
+        rhs_o2_element(m, &b, Q, e, out);
+        for (int n = 0; n < NF; ++n)
+            for (int t = 0; t < N3; ++t) R[qidx(m, n, e, 0, 0, 0) + t] = out[n * N3 + t];
+    }
+    return 0;
+}
+
+/* O2 restricted to a list of elements (for sampled checks of large meshes):
+ * R[n][s][k][j][i] for s = 0..nsel-1 is the right-hand side of element
+ * elems[s]. */
+int dgo_rhs_o2_elements(const dgo_mesh *m, const double *Q, int64_t nsel, const int64_t *elems,
+                        double *R)
+{
+    if (!mesh_ok(m) || !Q || !R || !elems || nsel < 0) return 1;
+    const int N = m->p + 1;
+    const int N3 = N * N * N;
+    for (int64_t s = 0; s < nsel; ++s)
+        if (elems[s] < 0 || elems[s] >= n_elem(m)) return 1;
+    basis1d b;
+    make_basis(N, &b);
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < nsel; ++s) {
+        double out[NF * NMAX * NMAX * NMAX];
+        rhs_o2_element(m, &b, Q, elems[s], out);
+        for (int n = 0; n < NF; ++n)
+            for (int t = 0; t < N3; ++t) R[((size_t)n * nsel + s) * N3 + t] = out[n * N3 + t];
     }
     return 0;
 }

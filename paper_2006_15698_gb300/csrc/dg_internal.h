@@ -1,0 +1,112 @@
+// dg_internal.h -- structures shared between the host API (dg_api.cu) and the
+// kernel translation units (dg_kernels_f64.cu, dg_kernels_f32.cu).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dg.h"
+
+namespace dg {
+
+constexpr int NF = 5;       // conserved fields (rho, rho u, rho v, rho w, rho E)
+constexpr int NMAX = DG_MAX_P + 1;
+
+// 1D operators of the collocated Gauss-Legendre basis, scaled by the
+// element geometry, in the kernels' scalar type.  Passed to kernels by value
+// (kernel parameter space), so every operand read is a constant-bank load.
+//   D[d][i][a]  = g_d * w_a l_i'(xi_a) / w_i    weak derivative with the
+//                                               inverse mass folded in
+//   Lp[d][i]    = g_d * l_i(+1) / w_i           lift of the +d face flux
+//   Lm[d][i]    = g_d * l_i(-1) / w_i           lift of the -d face flux
+//   lp[a], lm[a] = l_a(+1), l_a(-1)             trace interpolation
+// with g_d = 2 / h_d the reference-to-physical factor of direction d.
+template <typename real>
+struct Ops {
+    real D[3][NMAX][NMAX];
+    real Lp[3][NMAX];
+    real Lm[3][NMAX];
+    real lp[NMAX];
+    real lm[NMAX];
+};
+
+// Mesh geometry and sizes (plain values; also by value into kernels).
+struct Geo {
+    int nx, ny, nz, p;
+    long long E;       // elements
+    double x0, y0, z0;
+    double hx, hy, hz;
+    double gamma;
+    double J;          // hx hy hz / 8
+    double hmin;
+    double xi[NMAX];   // Gauss-Legendre nodes on [-1, 1]
+    double w[NMAX];    // Gauss-Legendre weights
+};
+
+// Per-kernel CUDA-event timing of a mesh handle (dg_profile_begin/end):
+// when on, every kernel launch is bracketed by two events recorded on the
+// launching stream; the pairs are summed per kernel kind on request.
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;   // start/stop pairs, in launch order
+    std::vector<int> kind;         // kernel kind of each pair
+    std::vector<cudaEvent_t> pool; // recycled events
+
+    cudaEvent_t take()
+    {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void start(int k, cudaStream_t s)
+    {
+        if (!on) return;
+        cudaEvent_t e = take();
+        cudaEventRecord(e, s);
+        ev.push_back(e);
+        kind.push_back(k);
+    }
+    void stop(cudaStream_t s)
+    {
+        if (!on) return;
+        cudaEvent_t e = take();
+        cudaEventRecord(e, s);
+        ev.push_back(e);
+    }
+};
+
+// Device workspace owned by a mesh handle.
+struct Work {
+    void *face_flux = nullptr;              // 3 * NF * E * N^2 scalars
+    double *partials = nullptr;             // norms partial sums, kNormBlocks x 8
+    unsigned long long *lam_bits = nullptr; // CFL maximum (bits of a positive double)
+    int *err = nullptr;                     // sticky error flag
+    Prof *prof = nullptr;                   // kernel timing (host object)
+};
+
+constexpr int kNormBlocks = 1024;  // fixed partition of the norms reduction
+
+// Launchers implemented per scalar type (dg_kernels_f64.cu / dg_kernels_f32.cu).
+// Each returns cudaSuccess or the launch error.
+template <typename real>
+struct Launch {
+    static cudaError_t init(const Geo &g, int kind, const double *params, real *Q, Work &w,
+                            cudaStream_t s);
+    static cudaError_t rhs(const Geo &g, const Ops<real> &ops, const real *Q, real *R, Work &w,
+                           cudaStream_t s);
+    static cudaError_t rk_step(const Geo &g, const Ops<real> &ops, real *Q, real *dQ,
+                               const double *dt, Work &w, cudaStream_t s);
+    static cudaError_t cfl(const Geo &g, const real *Q, double cfl, double *dt, Work &w,
+                           cudaStream_t s);
+    static cudaError_t norms(const Geo &g, const real *Q, const real *Qref, double *out, Work &w,
+                             cudaStream_t s);
+};
+
+}  // namespace dg

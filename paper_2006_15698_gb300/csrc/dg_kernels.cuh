@@ -1,0 +1,626 @@
+// dg_kernels.cuh -- sm_103a kernels of the DG Euler right-hand side and its
+// low-storage Runge-Kutta update, templated on the polynomial order and the
+// scalar type.  Included by one translation unit per scalar type.
+//
+// One right-hand-side evaluation (Sec. II.B, Eq. 5 with collocated
+// Gauss-Legendre quadrature) is two kernels:
+//
+//   face_flux_kernel   every unique face point of the mesh, once: the traces
+//                      of the two neighbouring elements' polynomials
+//                      (interpolated along the face-normal node line), and the
+//                      local Lax-Friedrichs flux between them -> flux buffer.
+//   volume_kernel      every node, once: the Euler flux vectors at the node
+//                      (Eq. 2-3), the sum-factorised weak derivative
+//                      sum_a D[i][a] F_a along each direction (staged through
+//                      shared memory), the lift of the six face fluxes, and
+//                      either the right-hand side itself or the RK stage
+//                      update of (dQ, Q) in place.
+//
+// Every floating-point operation of the method is done exactly once per
+// face point or node (no recomputation of traces or interface fluxes), which
+// is what matters on this GPU's narrow FP64 pipe.  The in-place stage update
+// is race-free because the only cross-element data of a stage (the interface
+// fluxes) is complete before volume_kernel starts.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+
+template <int N>
+struct Tile {
+    static constexpr int N2 = N * N;
+    static constexpr int N3 = N * N * N;
+    // elements per CTA of volume_kernel: about 256 threads (one per node)
+    static constexpr int EPB = N3 >= 128 ? 1 : (N3 >= 64 ? 4 : (256 / N3));
+    static constexpr int THREADS = ((EPB * N3 + 31) / 32) * 32;
+};
+
+// index of (field n, element e, in-element node) in a state array
+__device__ __forceinline__ long long sidx(int n, long long e, int node, long long E, int N3)
+{
+    return ((long long)n * E + e) * N3 + node;
+}
+
+// index in the interface-flux buffer F[d][n][e][face point]
+__device__ __forceinline__ long long fidx(int d, int n, long long e, int pt, long long E, int N2)
+{
+    return ((long long)(d * NF + n) * E + e) * N2 + pt;
+}
+
+// periodic neighbour of element e in direction DIR, side +1 or -1
+template <int DIR>
+__device__ __forceinline__ long long neighbour(long long e, int side, const Geo &g)
+{
+    const long long nx = g.nx, nxy = (long long)g.nx * g.ny;
+    if (DIR == 0) {
+        long long ex = e % nx;
+        if (side > 0) return ex == nx - 1 ? e - (nx - 1) : e + 1;
+        return ex == 0 ? e + (nx - 1) : e - 1;
+    } else if (DIR == 1) {
+        long long ey = (e / nx) % g.ny;
+        if (side > 0) return ey == g.ny - 1 ? e - (g.ny - 1) * nx : e + nx;
+        return ey == 0 ? e + (g.ny - 1) * nx : e - nx;
+    } else {
+        long long ez = e / nxy;
+        if (side > 0) return ez == g.nz - 1 ? e - (g.nz - 1) * nxy : e + nxy;
+        return ez == 0 ? e + (g.nz - 1) * nxy : e - nxy;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Euler physics (Eq. 2-3) and the local Lax-Friedrichs flux
+// ---------------------------------------------------------------------------
+
+// Normal flux F^DIR(q), its normal velocity magnitude + sound speed.
+template <int DIR, typename real>
+__device__ __forceinline__ void normal_flux(const real q[NF], real gamma, real gm1, real f[NF],
+                                           real &speed)
+{
+    const real rinv = real(1) / q[0];
+    const real mm = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    const real p = gm1 * (q[4] - real(0.5) * mm * rinv);
+    const real mn = q[1 + DIR];
+    const real un = mn * rinv;
+    f[0] = mn;
+    f[1] = q[1] * un + (DIR == 0 ? p : real(0));
+    f[2] = q[2] * un + (DIR == 1 ? p : real(0));
+    f[3] = q[3] * un + (DIR == 2 ? p : real(0));
+    f[4] = (q[4] + p) * un;
+    speed = fabs(un) + sqrt(gamma * p * rinv);
+}
+
+// Local Lax-Friedrichs (Rusanov) flux through a face with normal +e_DIR,
+// qL on the -side, qR on the +side (Sec. II.B; local dissipation speed):
+//   F* = (F(qL) + F(qR))/2 - max(|u_n| + c)/2 (qR - qL)
+template <int DIR, typename real>
+__device__ __forceinline__ void lf_flux(const real qL[NF], const real qR[NF], real gamma,
+                                        real gm1, real f[NF])
+{
+    real fL[NF], fR[NF], sL, sR;
+    normal_flux<DIR>(qL, gamma, gm1, fL, sL);
+    normal_flux<DIR>(qR, gamma, gm1, fR, sR);
+    const real hl = real(0.5) * fmax(sL, sR);
+#pragma unroll
+    for (int n = 0; n < NF; ++n) f[n] = real(0.5) * (fL[n] + fR[n]) - hl * (qR[n] - qL[n]);
+}
+
+// ---------------------------------------------------------------------------
+// interface fluxes
+// ---------------------------------------------------------------------------
+
+// One thread per (direction, element, face point) of the element's +DIR face.
+// Face point pt = t2*N + t1 where (t1, t2) are the two tangential node indices
+// in (i, j, k) order.  The element is the left state, its +DIR neighbour the
+// right state; each unique face of the periodic mesh is visited once.
+template <int N, int DIR, typename real>
+__device__ __forceinline__ void face_point(const real *__restrict__ Q, real *__restrict__ F,
+                                           const Ops<real> &T, const Geo &g, long long e, int pt)
+{
+    constexpr int N2 = N * N, N3 = N * N * N;
+    const int t1 = pt % N, t2 = pt / N;
+    const int base = DIR == 0 ? (t2 * N + t1) * N : (DIR == 1 ? t2 * N2 + t1 : t2 * N + t1);
+    constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? N : N2);
+    const long long en = neighbour<DIR>(e, +1, g);
+    real qL[NF], qR[NF];
+#pragma unroll
+    for (int n = 0; n < NF; ++n) {
+        const real *a = Q + sidx(n, e, base, g.E, N3);
+        const real *b = Q + sidx(n, en, base, g.E, N3);
+        real sl = real(0), sr = real(0);
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            sl += T.lp[c] * __ldg(a + c * stride);
+            sr += T.lm[c] * __ldg(b + c * stride);
+        }
+        qL[n] = sl;
+        qR[n] = sr;
+    }
+    real f[NF];
+    lf_flux<DIR>(qL, qR, real(g.gamma), real(g.gamma - 1.0), f);
+#pragma unroll
+    for (int n = 0; n < NF; ++n) F[fidx(DIR, n, e, pt, g.E, N2)] = f[n];
+}
+
+template <int N, typename real>
+__global__ void __launch_bounds__(256) face_flux_kernel(const real *__restrict__ Q,
+                                                        real *__restrict__ F, const Ops<real> T,
+                                                        const Geo g)
+{
+    constexpr int N2 = N * N;
+    const long long per_dir = g.E * N2;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * per_dir) return;
+    const int d = (int)(t / per_dir);
+    const long long r = t - d * per_dir;
+    const long long e = r / N2;
+    const int pt = (int)(r - e * N2);
+    if (d == 0) face_point<N, 0>(Q, F, T, g, e, pt);
+    else if (d == 1) face_point<N, 1>(Q, F, T, g, e, pt);
+    else face_point<N, 2>(Q, F, T, g, e, pt);
+}
+
+// ---------------------------------------------------------------------------
+// volume term, lift and stage update
+// ---------------------------------------------------------------------------
+
+// MODE 0: write R = dQ/dt.   MODE 1: LSERK stage, dQ <- A dQ + dt R,
+// Q <- Q + B dQ, in place (first stage: A == 0 and dQ is not read).
+template <int N, typename real, int MODE>
+__global__ void __launch_bounds__(Tile<N>::THREADS)
+    volume_kernel(const real *Qin, real *Out, real *dQ, const real *__restrict__ F,
+                  const Ops<real> T, const Geo g, real A, real B, const double *__restrict__ dt)
+{
+    constexpr int N2 = N * N, N3 = N * N * N, EPB = Tile<N>::EPB;
+    extern __shared__ unsigned char smem_raw[];
+    real *sF = reinterpret_cast<real *>(smem_raw);  // [EPB][3][NF][N3]
+
+    const int tid = threadIdx.x;
+    const int el = tid / N3;
+    const int node = tid - el * N3;
+    const long long e = (long long)blockIdx.x * EPB + el;
+    const bool active = el < EPB && e < g.E;
+    const int i = node % N, j = (node / N) % N, k = node / N2;
+
+    real q[NF];
+    if (active) {
+#pragma unroll
+        for (int n = 0; n < NF; ++n) q[n] = Qin[sidx(n, e, node, g.E, N3)];
+        // fluxes at this node (Eq. 2 with the closure of Eq. 3)
+        const real gm1 = real(g.gamma - 1.0);
+        const real rinv = real(1) / q[0];
+        const real u = q[1] * rinv, v = q[2] * rinv, w = q[3] * rinv;
+        const real p = gm1 * (q[4] - real(0.5) * (q[1] * u + q[2] * v + q[3] * w));
+        const real ep = q[4] + p;
+        real *s = sF + (size_t)el * 3 * NF * N3 + node;
+        s[(0 * NF + 0) * N3] = q[1];
+        s[(0 * NF + 1) * N3] = q[1] * u + p;
+        s[(0 * NF + 2) * N3] = q[2] * u;
+        s[(0 * NF + 3) * N3] = q[3] * u;
+        s[(0 * NF + 4) * N3] = ep * u;
+        s[(1 * NF + 0) * N3] = q[2];
+        s[(1 * NF + 1) * N3] = q[1] * v;
+        s[(1 * NF + 2) * N3] = q[2] * v + p;
+        s[(1 * NF + 3) * N3] = q[3] * v;
+        s[(1 * NF + 4) * N3] = ep * v;
+        s[(2 * NF + 0) * N3] = q[3];
+        s[(2 * NF + 1) * N3] = q[1] * w;
+        s[(2 * NF + 2) * N3] = q[2] * w;
+        s[(2 * NF + 3) * N3] = q[3] * w + p;
+        s[(2 * NF + 4) * N3] = ep * w;
+    }
+    __syncthreads();
+    if (!active) return;
+
+    const long long exm = neighbour<0>(e, -1, g);
+    const long long eym = neighbour<1>(e, -1, g);
+    const long long ezm = neighbour<2>(e, -1, g);
+    const int px = k * N + j, py = k * N + i, pz = j * N + i;
+    real dtr = real(0);
+    if (MODE == 1) dtr = real(*dt);
+
+#pragma unroll
+    for (int n = 0; n < NF; ++n) {
+        const real *sx = sF + ((size_t)el * 3 + 0) * NF * N3 + n * N3;
+        const real *sy = sF + ((size_t)el * 3 + 1) * NF * N3 + n * N3;
+        const real *sz = sF + ((size_t)el * 3 + 2) * NF * N3 + n * N3;
+        real acc = real(0);
+        // sum-factorised weak derivative along x, y, z
+#pragma unroll
+        for (int a = 0; a < N; ++a) acc += T.D[0][i][a] * sx[(k * N + j) * N + a];
+#pragma unroll
+        for (int b = 0; b < N; ++b) acc += T.D[1][j][b] * sy[(k * N + b) * N + i];
+#pragma unroll
+        for (int c = 0; c < N; ++c) acc += T.D[2][k][c] * sz[(c * N + j) * N + i];
+        // lift of the six interface fluxes (outward normal -> sign)
+        acc -= T.Lp[0][i] * __ldg(F + fidx(0, n, e, px, g.E, N2));
+        acc += T.Lm[0][i] * __ldg(F + fidx(0, n, exm, px, g.E, N2));
+        acc -= T.Lp[1][j] * __ldg(F + fidx(1, n, e, py, g.E, N2));
+        acc += T.Lm[1][j] * __ldg(F + fidx(1, n, eym, py, g.E, N2));
+        acc -= T.Lp[2][k] * __ldg(F + fidx(2, n, e, pz, g.E, N2));
+        acc += T.Lm[2][k] * __ldg(F + fidx(2, n, ezm, pz, g.E, N2));
+
+        const long long o = sidx(n, e, node, g.E, N3);
+        if (MODE == 0) {
+            Out[o] = acc;
+        } else {
+            const real d = (A == real(0) ? real(0) : A * dQ[o]) + dtr * acc;
+            dQ[o] = d;
+            Out[o] = q[n] + B * d;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// time step, integrals, initial states
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Lambda = max over nodes of sum_d (|u_d| + c), in double; a node with
+// rho <= 0, p <= 0 or NaN contributes a NaN whose bit pattern is above every
+// finite value, and raises the error flag.
+template <typename real>
+__global__ void __launch_bounds__(256) cfl_kernel(const real *__restrict__ Q, long long nodes,
+                                                  double gamma, unsigned long long *lam_bits,
+                                                  int *err)
+{
+    double m = 0.0;
+    bool bad = false;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nodes;
+         t += (long long)gridDim.x * blockDim.x) {
+        // every operation explicitly rounded (no FMA contraction), in a fixed
+        // order, so the wave speed of a node is the same double on any
+        // conforming implementation of IEEE-754 arithmetic
+        const double r = (double)Q[t], mx = (double)Q[nodes + t], my = (double)Q[2 * nodes + t],
+                     mz = (double)Q[3 * nodes + t], E = (double)Q[4 * nodes + t];
+        const double u = __ddiv_rn(mx, r), v = __ddiv_rn(my, r), w = __ddiv_rn(mz, r);
+        const double uu = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
+        const double p = __dmul_rn(gamma - 1.0, __dsub_rn(E, __dmul_rn(__dmul_rn(0.5, r), uu)));
+        if (!(r > 0.0) || !(p > 0.0)) {
+            bad = true;
+            continue;
+        }
+        const double c = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), r));
+        const double s = __dadd_rn(__dadd_rn(__dadd_rn(fabs(u), c), __dadd_rn(fabs(v), c)),
+                                   __dadd_rn(fabs(w), c));
+        m = fmax(m, s);
+    }
+    if (bad) {
+        atomicOr(err, 1);
+        m = __longlong_as_double(0x7ff8000000000000LL);
+    }
+    // NaN-propagating max over the block: compare bit patterns of non-negative doubles
+    unsigned long long b = (unsigned long long)__double_as_longlong(m);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long x = __shfl_xor_sync(0xffffffffu, b, o);
+        b = x > b ? x : b;
+    }
+    __shared__ unsigned long long redb[8];
+    if ((threadIdx.x & 31) == 0) redb[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long mb = redb[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mb = redb[w] > mb ? redb[w] : mb;
+        atomicMax(lam_bits, mb);
+    }
+}
+
+static __global__ void cfl_finalize_kernel(unsigned long long *lam_bits, double cfl, double hmin,
+                                    int p, double *dt)
+{
+    const double lam = __longlong_as_double((long long)*lam_bits);
+    *dt = __ddiv_rn(__dmul_rn(cfl, hmin), __dmul_rn(2.0 * p + 1.0, lam));
+    *lam_bits = 0ull;  // ready for the next reduction on this stream
+}
+
+// Pass 1 of the integrals: block b sums a fixed contiguous range of nodes in a
+// fixed order (thread-strided, then a shared-memory tree), so the result does
+// not depend on scheduling.  Values: I_0..I_4, KE, |Q-Qref|^2, |Qref|^2.
+template <typename real>
+__global__ void __launch_bounds__(256) norms_partial_kernel(const real *__restrict__ Q,
+                                                            const real *__restrict__ Qref,
+                                                            const Geo g, double *partials)
+{
+    __shared__ double red[8][256];
+    const int N = g.p + 1, N3 = N * N * N;
+    const long long nodes = g.E * N3;
+    const long long chunk = (nodes + gridDim.x - 1) / gridDim.x;
+    const long long beg = (long long)blockIdx.x * chunk;
+    const long long end = beg + chunk < nodes ? beg + chunk : nodes;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long t = beg + threadIdx.x; t < end; t += blockDim.x) {
+        const int node = (int)(t % N3);
+        const int i = node % N, j = (node / N) % N, k = node / (N * N);
+        const double wq = g.J * (g.w[i] * g.w[j] * g.w[k]);
+        double q[NF];
+#pragma unroll
+        for (int n = 0; n < NF; ++n) q[n] = (double)Q[n * nodes + t];
+#pragma unroll
+        for (int n = 0; n < NF; ++n) acc[n] += wq * q[n];
+        acc[5] += wq * 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0];
+        if (Qref) {
+#pragma unroll
+            for (int n = 0; n < NF; ++n) {
+                const double r = (double)Qref[n * nodes + t];
+                acc[6] += wq * (q[n] - r) * (q[n] - r);
+                acc[7] += wq * r * r;
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) red[v][threadIdx.x] = acc[v];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) partials[blockIdx.x * 8 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Pass 2: one block sums the partials in a fixed order.
+static __global__ void __launch_bounds__(256) norms_final_kernel(const double *__restrict__ partials,
+                                                          int nblocks, int has_ref, double *out)
+{
+    __shared__ double red[8][256];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[v] += partials[b * 8 + v];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) red[v][threadIdx.x] = acc[v];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int v = 0; v < 6; ++v) out[v] = red[v][0];
+        out[6] = has_ref ? sqrt(red[6][0]) / sqrt(red[7][0]) : 0.0;
+    }
+}
+
+// Initial states at the nodes (kinds of dg_init_kind), evaluated in double.
+struct InitParams {
+    double v[8];
+};
+
+template <typename real>
+__global__ void __launch_bounds__(256) init_kernel(const Geo g, int kind, const InitParams prm,
+                                                   real *__restrict__ Q)
+{
+    const int N = g.p + 1, N3 = N * N * N;
+    const long long nodes = g.E * N3;
+    const double pi = 3.14159265358979323846;
+    const double gam = g.gamma;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nodes;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long e = t / N3;
+        const int node = (int)(t - e * N3);
+        const int i = node % N, j = (node / N) % N, k = node / (N * N);
+        const long long ex = e % g.nx, ey = (e / g.nx) % g.ny, ez = e / ((long long)g.nx * g.ny);
+        const double x = g.x0 + ((double)ex + 0.5 * (g.xi[i] + 1.0)) * g.hx;
+        const double y = g.y0 + ((double)ey + 0.5 * (g.xi[j] + 1.0)) * g.hy;
+        const double z = g.z0 + ((double)ez + 0.5 * (g.xi[k] + 1.0)) * g.hz;
+        double rho, u, v, w, p;
+        if (kind == DG_INIT_UNIFORM) {
+            rho = prm.v[0]; u = prm.v[1]; v = prm.v[2]; w = prm.v[3]; p = prm.v[4];
+        } else if (kind == DG_INIT_VORTEX) {
+            const double beta = prm.v[0], tt = prm.v[6];
+            const double Lx = g.hx * g.nx, Ly = g.hy * g.ny;
+            double dx = x - prm.v[1] - prm.v[3] * tt;
+            double dy = y - prm.v[2] - prm.v[4] * tt;
+            dx -= Lx * round(dx / Lx);  // minimum image on the periodic box
+            dy -= Ly * round(dy / Ly);
+            const double r2 = dx * dx + dy * dy;
+            const double ex1 = exp(0.5 * (1.0 - r2));
+            u = prm.v[3] - beta / (2.0 * pi) * dy * ex1;
+            v = prm.v[4] + beta / (2.0 * pi) * dx * ex1;
+            w = prm.v[5];
+            const double T = 1.0 - (gam - 1.0) * beta * beta / (8.0 * gam * pi * pi) * exp(1.0 - r2);
+            rho = pow(T, 1.0 / (gam - 1.0));
+            p = pow(rho, gam);
+        } else {
+            const double rho0 = prm.v[0], V0 = prm.v[1], Ma = prm.v[2];
+            const double p0 = rho0 * V0 * V0 / (gam * Ma * Ma);
+            u = V0 * sin(x) * cos(y) * cos(z);
+            v = -V0 * cos(x) * sin(y) * cos(z);
+            w = 0.0;
+            p = p0 + rho0 * V0 * V0 / 16.0 * (cos(2.0 * x) + cos(2.0 * y)) * (cos(2.0 * z) + 2.0);
+            rho = rho0 * p / p0;
+        }
+        Q[t] = (real)rho;
+        Q[nodes + t] = (real)(rho * u);
+        Q[2 * nodes + t] = (real)(rho * v);
+        Q[3 * nodes + t] = (real)(rho * w);
+        Q[4 * nodes + t] = (real)(p / (gam - 1.0) + 0.5 * rho * (u * u + v * v + w * w));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+// Carpenter & Kennedy (1994) five-stage fourth-order 2N-storage coefficients.
+constexpr double kRkA[5] = {0.0,
+                            -567301805773.0 / 1357537059087.0,
+                            -2404267990393.0 / 2016746695238.0,
+                            -3550918686646.0 / 2091501179385.0,
+                            -1275806237668.0 / 842570457699.0};
+constexpr double kRkB[5] = {1432997174477.0 / 9575080441755.0,
+                            5161836677717.0 / 13612068292357.0,
+                            1720146321549.0 / 2090206949498.0,
+                            3134564353537.0 / 4481467310338.0,
+                            2277821191437.0 / 14882151754819.0};
+
+inline int grid_for(long long n, int threads, long long cap)
+{
+    long long b = (n + threads - 1) / threads;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// kernel kinds of the per-kernel timing (dg_profile_end)
+enum { kKindFace = 0, kKindVolume = 1, kKindCfl = 2, kKindNorms = 3, kKindInit = 4 };
+
+struct ProfScope {
+    Prof *p;
+    cudaStream_t s;
+    ProfScope(Prof *p_, int kind, cudaStream_t s_) : p(p_), s(s_)
+    {
+        if (p) p->start(kind, s);
+    }
+    ~ProfScope()
+    {
+        if (p) p->stop(s);
+    }
+};
+
+constexpr long long kMaxGridX = 2147483647LL;
+
+template <int N, typename real>
+cudaError_t launch_face(const Geo &g, const Ops<real> &T, const real *Q, real *F, Prof *prof,
+                        cudaStream_t s)
+{
+    const long long n = 3 * g.E * (long long)(N * N);
+    const long long blocks = (n + 255) / 256;
+    if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
+    ProfScope ps(prof, kKindFace, s);
+    face_flux_kernel<N, real><<<(unsigned)blocks, 256, 0, s>>>(Q, F, T, g);
+    return cudaGetLastError();
+}
+
+template <int N, typename real, int MODE>
+cudaError_t launch_volume(const Geo &g, const Ops<real> &T, const real *Qin, real *Out, real *dQ,
+                          const real *F, real A, real B, const double *dt, Prof *prof,
+                          cudaStream_t s)
+{
+    constexpr int EPB = Tile<N>::EPB, THREADS = Tile<N>::THREADS, N3 = N * N * N;
+    const size_t smem = (size_t)EPB * 3 * NF * N3 * sizeof(real);
+    if (smem > 48 * 1024) {  // opt in above the default dynamic shared-memory limit
+        cudaError_t err = cudaFuncSetAttribute(volume_kernel<N, real, MODE>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+        if (err != cudaSuccess) return err;
+    }
+    const long long blocks = (g.E + EPB - 1) / EPB;
+    if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
+    ProfScope ps(prof, kKindVolume, s);
+    volume_kernel<N, real, MODE><<<(unsigned)blocks, THREADS, smem, s>>>(Qin, Out, dQ, F, T, g, A,
+                                                                          B, dt);
+    return cudaGetLastError();
+}
+
+template <int N, typename real>
+cudaError_t rhs_n(const Geo &g, const Ops<real> &T, const real *Q, real *R, Work &w,
+                  cudaStream_t s)
+{
+    real *F = static_cast<real *>(w.face_flux);
+    cudaError_t err = launch_face<N>(g, T, Q, F, w.prof, s);
+    if (err != cudaSuccess) return err;
+    return launch_volume<N, real, 0>(g, T, Q, R, nullptr, F, real(0), real(0), nullptr, w.prof,
+                                     s);
+}
+
+template <int N, typename real>
+cudaError_t rk_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, const double *dt, Work &w,
+                 cudaStream_t s)
+{
+    real *F = static_cast<real *>(w.face_flux);
+    for (int st = 0; st < 5; ++st) {
+        cudaError_t err = launch_face<N>(g, T, Q, F, w.prof, s);
+        if (err != cudaSuccess) return err;
+        err = launch_volume<N, real, 1>(g, T, Q, Q, dQ, F, real(kRkA[st]), real(kRkB[st]), dt,
+                                        w.prof, s);
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+#define DG_DISPATCH_P(p, CALL)            \
+    switch (p) {                          \
+    case 0: return CALL(1);               \
+    case 1: return CALL(2);               \
+    case 2: return CALL(3);               \
+    case 3: return CALL(4);               \
+    case 4: return CALL(5);               \
+    case 5: return CALL(6);               \
+    case 6: return CALL(7);               \
+    default: return cudaErrorInvalidValue; \
+    }
+
+template <typename real>
+cudaError_t Launch<real>::rhs(const Geo &g, const Ops<real> &T, const real *Q, real *R, Work &w,
+                              cudaStream_t s)
+{
+#define DG_CALL(NN) rhs_n<NN, real>(g, T, Q, R, w, s)
+    DG_DISPATCH_P(g.p, DG_CALL)
+#undef DG_CALL
+}
+
+template <typename real>
+cudaError_t Launch<real>::rk_step(const Geo &g, const Ops<real> &T, real *Q, real *dQ,
+                                  const double *dt, Work &w, cudaStream_t s)
+{
+#define DG_CALL(NN) rk_n<NN, real>(g, T, Q, dQ, dt, w, s)
+    DG_DISPATCH_P(g.p, DG_CALL)
+#undef DG_CALL
+}
+
+template <typename real>
+cudaError_t Launch<real>::cfl(const Geo &g, const real *Q, double cfl, double *dt, Work &w,
+                              cudaStream_t s)
+{
+    const int N = g.p + 1;
+    const long long nodes = g.E * N * N * N;
+    ProfScope ps(w.prof, kKindCfl, s);
+    cfl_kernel<real><<<grid_for(nodes, 256, 152 * 8), 256, 0, s>>>(Q, nodes, g.gamma, w.lam_bits,
+                                                                    w.err);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    cfl_finalize_kernel<<<1, 1, 0, s>>>(w.lam_bits, cfl, g.hmin, g.p, dt);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t Launch<real>::norms(const Geo &g, const real *Q, const real *Qref, double *out,
+                                Work &w, cudaStream_t s)
+{
+    ProfScope ps(w.prof, kKindNorms, s);
+    norms_partial_kernel<real><<<kNormBlocks, 256, 0, s>>>(Q, Qref, g, w.partials);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    norms_final_kernel<<<1, 256, 0, s>>>(w.partials, kNormBlocks, Qref != nullptr, out);
+    return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t Launch<real>::init(const Geo &g, int kind, const double *params, real *Q, Work &w,
+                               cudaStream_t s)
+{
+    InitParams prm{};  // params: 8 doubles, zero-padded by the caller
+    for (int i = 0; i < 8; ++i) prm.v[i] = params[i];
+    const int N = g.p + 1;
+    const long long nodes = g.E * N * N * N;
+    ProfScope ps(w.prof, kKindInit, s);
+    init_kernel<real><<<grid_for(nodes, 256, 152 * 16), 256, 0, s>>>(g, kind, prm, Q);
+    return cudaGetLastError();
+}
+
+}  // namespace dg

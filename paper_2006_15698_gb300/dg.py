@@ -1,0 +1,223 @@
+"""ctypes binding of the C ABI in include/dg.h (argument marshalling only).
+
+Every step of the computation runs in the CUDA library
+``paper_2006_15698_gb300/lib/libdg_gb300.so``; this module only turns torch
+tensors into device pointers and the current torch stream into the
+``stream`` argument.  Importing it raises if the library has not been built
+(``python -c "import __graft_entry__ as g; g.build()"``): there is no CPU
+fallback.
+
+The functions named ``dg_*`` mirror the C entry points one to one; ``Mesh``
+is a small convenience wrapper over them.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libdg_gb300.so")
+
+DG_OK, DG_ERR_ARG, DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NONFINITE, \
+    DG_ERR_BOUNDS, DG_ERR_TIMEOUT = range(8)
+DG_FP64, DG_FP32 = 0, 1
+DG_INIT_UNIFORM, DG_INIT_VORTEX, DG_INIT_TGV = 0, 1, 2
+DG_MAX_P = 6
+DG_NORMS_LEN = 7
+NF = 5
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"CUDA library not built: {LIB_PATH} is missing "
+                      "(run paper_2006_15698_gb300/build.py or __graft_entry__.build())")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_szp = ctypes.POINTER(ctypes.c_size_t)
+
+_lib.dg_mesh_create.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double] * 7 + [
+    ctypes.c_int, ctypes.POINTER(_vp)]
+_lib.dg_mesh_create.restype = ctypes.c_int
+_lib.dg_mesh_destroy.argtypes = [_vp]
+_lib.dg_mesh_destroy.restype = None
+_lib.dg_mesh_sizes.argtypes = [_vp, _i64p, _i64p, _szp, _szp]
+_lib.dg_mesh_sizes.restype = ctypes.c_int
+_lib.dg_state_init.argtypes = [_vp, ctypes.c_int, _dp, ctypes.c_int, _vp, _vp]
+_lib.dg_state_init.restype = ctypes.c_int
+_lib.dg_rhs.argtypes = [_vp, _vp, _vp, _vp]
+_lib.dg_rhs.restype = ctypes.c_int
+_lib.dg_cfl_dt.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp]
+_lib.dg_cfl_dt.restype = ctypes.c_int
+_lib.dg_rk_step.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.dg_rk_step.restype = ctypes.c_int
+_lib.dg_norms.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.dg_norms.restype = ctypes.c_int
+_lib.dg_status_string.argtypes = [ctypes.c_int]
+_lib.dg_status_string.restype = ctypes.c_char_p
+_lib.dg_last_error.argtypes = [_vp]
+_lib.dg_last_error.restype = ctypes.c_int
+_lib.dg_profile_begin.argtypes = [_vp]
+_lib.dg_profile_begin.restype = ctypes.c_int
+_lib.dg_profile_end.argtypes = [_vp, _dp, _i64p]
+_lib.dg_profile_end.restype = ctypes.c_int
+
+DG_PROFILE_KINDS = 5
+KERNEL_KINDS = ("face", "volume", "cfl", "norms", "init")
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {dg_status_string(status)} ({status})")
+
+
+def _check(st, where):
+    if st != DG_OK:
+        raise DGError(st, where)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+# --- one-to-one mirrors of the C entry points ------------------------------
+
+def dg_mesh_create(nx, ny, nz, p, x0, y0, z0, Lx, Ly, Lz, gamma, precision):
+    h = _vp()
+    _check(_lib.dg_mesh_create(nx, ny, nz, p, x0, y0, z0, Lx, Ly, Lz, gamma, precision,
+                               ctypes.byref(h)), "dg_mesh_create")
+    return h
+
+
+def dg_mesh_destroy(h):
+    _lib.dg_mesh_destroy(h)
+
+
+def dg_mesh_sizes(h):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    c, d = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(_lib.dg_mesh_sizes(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                              ctypes.byref(d)), "dg_mesh_sizes")
+    return a.value, b.value, c.value, d.value
+
+
+def dg_state_init(h, kind, params, Q, stream=None):
+    arr = (ctypes.c_double * len(params))(*[float(x) for x in params])
+    _check(_lib.dg_state_init(h, kind, arr, len(params), _ptr(Q), _stream(stream)),
+           "dg_state_init")
+
+
+def dg_rhs(h, Q, R, stream=None):
+    _check(_lib.dg_rhs(h, _ptr(Q), _ptr(R), _stream(stream)), "dg_rhs")
+
+
+def dg_cfl_dt(h, Q, cfl, dt_dev, stream=None):
+    _check(_lib.dg_cfl_dt(h, _ptr(Q), float(cfl), _ptr(dt_dev), _stream(stream)), "dg_cfl_dt")
+
+
+def dg_rk_step(h, Q, dQ, dt_dev, stream=None):
+    _check(_lib.dg_rk_step(h, _ptr(Q), _ptr(dQ), _ptr(dt_dev), _stream(stream)), "dg_rk_step")
+
+
+def dg_norms(h, Q, Qref, out_dev, stream=None):
+    _check(_lib.dg_norms(h, _ptr(Q), _ptr(Qref), _ptr(out_dev), _stream(stream)), "dg_norms")
+
+
+def dg_status_string(st):
+    return _lib.dg_status_string(st).decode()
+
+
+def dg_last_error(h):
+    return _lib.dg_last_error(h)
+
+
+def dg_profile_begin(h):
+    _check(_lib.dg_profile_begin(h), "dg_profile_begin")
+
+
+def dg_profile_end(h):
+    ms = (ctypes.c_double * DG_PROFILE_KINDS)()
+    n = (ctypes.c_int64 * DG_PROFILE_KINDS)()
+    _check(_lib.dg_profile_end(h, ms, n), "dg_profile_end")
+    return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+# --- convenience wrapper ---------------------------------------------------
+
+class Mesh:
+    """A periodic Cartesian mesh handle; states are torch tensors on the GPU
+    with shape (5, elements, N, N, N) (the ABI layout), dtype float64 for
+    DG_FP64 and float32 for DG_FP32."""
+
+    def __init__(self, nx, ny, nz, p, x0=0.0, y0=0.0, z0=0.0, Lx=1.0, Ly=1.0, Lz=1.0,
+                 gamma=1.4, precision=DG_FP64, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        with torch.cuda.device(self.device):
+            self.h = dg_mesh_create(nx, ny, nz, p, x0, y0, z0, Lx, Ly, Lz, gamma, precision)
+        self.nx, self.ny, self.nz, self.p = nx, ny, nz, p
+        self.N = p + 1
+        self.E = nx * ny * nz
+        self.precision = precision
+        self.dtype = torch.float64 if precision == DG_FP64 else torch.float32
+        self.n_dof, self.n_unknowns, self.state_bytes, self.workspace_bytes = dg_mesh_sizes(self.h)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            dg_mesh_destroy(h)
+            self.h = None
+
+    @property
+    def shape(self):
+        return (NF, self.E, self.N, self.N, self.N)
+
+    def empty(self):
+        return torch.empty(self.shape, dtype=self.dtype, device=self.device)
+
+    def _chk(self, t):
+        if (t.dtype != self.dtype or not t.is_cuda or not t.is_contiguous()
+                or (tuple(t.shape) != self.shape and t.numel() != NF * self.n_dof)):
+            raise ValueError("state tensor must be a contiguous CUDA tensor of the mesh's "
+                             f"shape {self.shape} and dtype {self.dtype}")
+        return t
+
+    def init(self, kind, params, Q=None, stream=None):
+        kinds = {"uniform": DG_INIT_UNIFORM, "vortex": DG_INIT_VORTEX, "tgv": DG_INIT_TGV}
+        Q = self.empty() if Q is None else self._chk(Q)
+        dg_state_init(self.h, kinds.get(kind, kind), params, Q, stream)
+        return Q
+
+    def rhs(self, Q, R=None, stream=None):
+        R = self.empty() if R is None else self._chk(R)
+        dg_rhs(self.h, self._chk(Q), R, stream)
+        return R
+
+    def cfl_dt(self, Q, cfl, dt=None, stream=None):
+        dt = torch.empty(1, dtype=torch.float64, device=self.device) if dt is None else dt
+        dg_cfl_dt(self.h, self._chk(Q), cfl, dt, stream)
+        return dt
+
+    def rk_step(self, Q, dQ, dt, stream=None):
+        dg_rk_step(self.h, self._chk(Q), self._chk(dQ), dt, stream)
+
+    def norms(self, Q, Qref=None, out=None, stream=None):
+        out = torch.empty(DG_NORMS_LEN, dtype=torch.float64, device=self.device) if out is None else out
+        dg_norms(self.h, self._chk(Q), None if Qref is None else self._chk(Qref), out, stream)
+        return out
+
+    def last_error(self):
+        return dg_last_error(self.h)
+
+    def profile_begin(self):
+        dg_profile_begin(self.h)
+
+    def profile_end(self):
+        """{kind: (summed device ms, launches)} since profile_begin."""
+        return dg_profile_end(self.h)

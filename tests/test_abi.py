@@ -1,0 +1,75 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/dg.h declares, and rejects bad arguments on the
+host before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dg.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2006_15698_gb300.build import build
+    return ctypes.CDLL(build())
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dg_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert "dg_rk_step" in names and len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in dg.h but not exported"
+
+
+def test_status_strings(lib):
+    lib.dg_status_string.restype = ctypes.c_char_p
+    for s in range(8):
+        assert lib.dg_status_string(s)
+    assert lib.dg_status_string(99) == b"unknown status"
+
+
+def _create(lib, *a):
+    h = ctypes.c_void_p()
+    f = lib.dg_mesh_create
+    f.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double] * 7 + [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    f.restype = ctypes.c_int
+    st = f(*a, ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("args,status", [
+    ((0, 1, 1, 2, 0, 0, 0, 1, 1, 1, 1.4, 0), 1),      # nx = 0
+    ((1, 1, 1, 2, 0, 0, 0, -1, 1, 1, 1.4, 0), 1),     # Lx < 0
+    ((1, 1, 1, 2, 0, 0, 0, 1, 1, 1, 1.0, 0), 1),      # gamma <= 1
+    ((1, 1, 1, 2, 0, 0, 0, 1, 1, 1, 1.4, 7), 1),      # bad precision
+    ((1, 1, 1, 7, 0, 0, 0, 1, 1, 1, 1.4, 0), 2),      # p > 6
+    ((1, 1, 1, -1, 0, 0, 0, 1, 1, 1, 1.4, 0), 2),     # p < 0
+    ((1 << 14, 1 << 14, 1 << 14, 6, 0, 0, 0, 1, 1, 1, 1.4, 0), 1),  # too many nodes
+    ((1, 1, 1, 2, float("nan"), 0, 0, 1, 1, 1, 1.4, 0), 1),
+])
+def test_mesh_create_rejects_bad_arguments_on_host(lib, args, status):
+    st, h = _create(lib, *args)
+    assert st == status and not h.value
+
+
+def test_null_handles_rejected(lib):
+    for name, nargs in [("dg_rhs", 4), ("dg_rk_step", 5), ("dg_norms", 5), ("dg_cfl_dt", 5)]:
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int
+        if name == "dg_cfl_dt":
+            f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+            assert f(None, None, 0.5, None, None) == 1
+        else:
+            f.argtypes = [ctypes.c_void_p] * nargs
+            assert f(*([None] * nargs)) == 1
+    lib.dg_mesh_destroy.argtypes = [ctypes.c_void_p]
+    lib.dg_mesh_destroy(None)  # NULL is ignored
