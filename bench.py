@@ -59,7 +59,7 @@ FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.070e9 / 1e12  # 128 FP32 FMA lanes/SM at ma
 
 def kernel_flops(kind, N, E):
     """Algorithmic flops per launch of the kernels (FMA = 2, div = sqrt = 1),
-    counted from the arithmetic they execute ("Kernels")."""
+    counted from the arithmetic the kernels execute per node / face point."""
     if kind == "volume":  # flux 28 + contraction 30N + lift 60 + RK update 25, per node
         return E * N ** 3 * (113 + 30 * N)
     if kind == "face":  # traces 20N + Lax-Friedrichs 69, per unique face point
@@ -135,6 +135,23 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def whole_job_rate(ms_local, units_local, device="cpu"):
+    """Whole-job throughput over all ranks: the units every rank processed
+    divided by the slowest rank's time (max over ranks).  Returns
+    (units/s, max ms).  Single process: no collective."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local), float(units_local)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        tm = t[:1].clone()
+        tu = t[1:].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tu, op=dist.ReduceOp.SUM)
+        t = torch.cat([tm, tu])
+    ms_max, units = float(t[0].item()), float(t[1].item())
+    return units / (ms_max / 1e3), ms_max
 
 
 def _dist():
@@ -289,12 +306,8 @@ def run_native(args, w):
     ck = clocks.stop()
     err = m.last_error()
 
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     dof = E * N ** 3
-    value = dof * 5 * args.steps * ws / (ms_max / 1e3)
+    value, ms_max = whole_job_rate(ms, dof * 5 * args.steps, device="cuda")
 
     # ---- end-to-end through host buffers: H2D state, step, D2H state + integrals
     e2e_steps = max(1, min(args.steps, 10))
@@ -314,10 +327,7 @@ def run_native(args, w):
         integ_h.copy_(integ, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
-    e2e_val = dof * 5 * e2e_steps * ws / (float(e2e_ms.item()) / 1e3)
+    e2e_val, _ = whole_job_rate(e0.elapsed_time(e1), dof * 5 * e2e_steps, device="cuda")
 
     out = None
     if rank == 0:

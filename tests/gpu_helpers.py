@@ -1,5 +1,5 @@
 """Shared helpers of the GPU parity tests: device round trips and the
-tolerance scales derived in DESIGN.md (section "Parity tolerances")."""
+scale the tolerances are measured against."""
 import numpy as np
 import pytest
 

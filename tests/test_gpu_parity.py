@@ -3,7 +3,7 @@ same seeded inputs.  Inputs are generated on the host (oracle initial states
 or the seeded generator) and uploaded; nothing the GPU computes feeds the
 oracle.
 
-Bars (derived in DESIGN.md, "Parity tolerances"):
+Bars:
   * one LSERK45 step, FP64: relative L2 of the new state <= 1e-12
   * right-hand side, FP64: ||dR|| <= 1e-12 * rhs_scale (the size of the
     terms being summed; see gpu_helpers.rhs_scale)
