@@ -60,7 +60,9 @@ typedef enum {
     DG_ERR_CUDA = 4,        /* a CUDA call or kernel launch failed */
     DG_ERR_NONFINITE = 5,   /* a kernel met rho <= 0, p <= 0 or a NaN (device flag) */
     DG_ERR_BOUNDS = 6,      /* reserved: an index check in a checking build failed */
-    DG_ERR_TIMEOUT = 7      /* reserved: a bounded wait ran out */
+    DG_ERR_TIMEOUT = 7,     /* reserved: a bounded wait ran out */
+    DG_ERR_TOO_LARGE = 8    /* the problem does not fit the fixed static scratch of
+                               dg_rhs_static (DG_STATIC_SCRATCH_BYTES) */
 } dg_status;
 
 typedef enum {
@@ -173,6 +175,46 @@ enum { DG_KERNEL_FACE = 0, DG_KERNEL_VOLUME = 1, DG_KERNEL_CFL = 2, DG_KERNEL_NO
        DG_KERNEL_INIT = 4 };
 dg_status dg_profile_begin(dg_mesh *mesh);
 dg_status dg_profile_end(dg_mesh *mesh, double *ms, int64_t *launches);
+
+/* Allocation-free right-hand side (the paper has no counterpart).
+ *
+ * Some callers cannot let a library allocate device memory: code that runs
+ * under a fixed device-memory budget, or inside a host framework whose own
+ * allocator already holds the free memory and forbids allocations by
+ * plugins.  Such callers cannot create a dg_mesh, because dg_mesh_create
+ * allocates the handle's workspace.  This entry point evaluates the same
+ * dQ/dt as dg_rhs for the mesh its arguments describe (the arguments mean what
+ * they mean for dg_mesh_create) without allocating or freeing anything: the
+ * 1D operators are computed on the host on every call, and the interface-
+ * flux scratch lives in one static device array of DG_STATIC_SCRATCH_BYTES
+ * (16 MiB) that every GPU which loads this library holds until the process
+ * exits.  Q and R are caller-owned device states in the layout above, double
+ * for DG_FP64 and float for DG_FP32; R must not overlap Q.
+ *
+ * Size limit: the interface fluxes take 15 * nx*ny*nz*(p+1)^2 scalars; a
+ * mesh that needs more than DG_STATIC_SCRATCH_BYTES is rejected with
+ * DG_ERR_TOO_LARGE before anything is enqueued (e.g. p = 4 in double fits up
+ * to 5,592 elements, 16^3 = 4,096 does; float doubles that).
+ *
+ * Set-up: the first call on each device looks up the device address of the
+ * static array (cudaGetSymbolAddress, with that device current) and keeps
+ * it; make that first call before any stream capture.
+ *
+ * Sharing: every call uses the same array, which keeps whatever the last call
+ * left in it (each call writes the part it reads before reading it, so
+ * nothing needs clearing).  Calls whose GPU work can overlap -- issued on
+ * different streams, or from several host threads -- race on the array; the
+ * caller must order them.
+ *
+ * Errors: DG_ERR_ARG / DG_ERR_UNSUPPORTED for the argument checks of
+ * dg_mesh_create and dg_rhs, DG_ERR_TOO_LARGE as above, DG_ERR_CUDA if the
+ * set-up or a launch fails. */
+#define DG_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+dg_status dg_rhs_static(int nx, int ny, int nz, int p,
+                        double x0, double y0, double z0,
+                        double Lx, double Ly, double Lz,
+                        double gamma, dg_precision precision,
+                        const void *Q, void *R, void *stream);
 
 /* Static text for a status code. */
 const char *dg_status_string(dg_status status);

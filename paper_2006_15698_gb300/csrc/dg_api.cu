@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "dg_internal.h"
@@ -304,6 +305,92 @@ dg_status dg_norms(const dg_mesh *m, const void *Q, const void *Qref, double *ou
     return cuda_status(e);
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// dg_rhs_static: the right-hand side without any device allocation.  The
+// interface-flux scratch is this file-scope device array; host code must not
+// use its name as a device address (on the host it names a stand-in), so
+// each device's address is looked up once with cudaGetSymbolAddress and
+// passed to the kernels.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_static_face_scratch[DG_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void *g_static_addr[kMaxDevices] = {};  // per device, filled on first use
+
+cudaError_t static_scratch_address(void **out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_face_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_rhs_static(int nx, int ny, int nz, int p, double x0, double y0, double z0,
+                        double Lx, double Ly, double Lz, double gamma, dg_precision precision,
+                        const void *Q, void *R, void *stream)
+{
+    if (!Q || !R || Q == R) return DG_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1) return DG_ERR_ARG;
+    if (!finite_pos(Lx) || !finite_pos(Ly) || !finite_pos(Lz)) return DG_ERR_ARG;
+    if (!std::isfinite(x0) || !std::isfinite(y0) || !std::isfinite(z0)) return DG_ERR_ARG;
+    if (!(std::isfinite(gamma) && gamma > 1.0)) return DG_ERR_ARG;
+    if (precision != DG_FP64 && precision != DG_FP32) return DG_ERR_ARG;
+    if (p < 0 || p > DG_MAX_P) return DG_ERR_UNSUPPORTED;
+    const int N = p + 1;
+    const long long E = (long long)nx * ny * nz;
+    if (E * N * N * N >= (1LL << 40)) return DG_ERR_ARG;
+    const size_t esz = precision == DG_FP64 ? sizeof(double) : sizeof(float);
+    const double need = 3.0 * dg::NF * (double)E * N * N * (double)esz;
+    if (need > (double)DG_STATIC_SCRATCH_BYTES) return DG_ERR_TOO_LARGE;
+
+    dg::Geo g{};
+    g.nx = nx; g.ny = ny; g.nz = nz; g.p = p; g.E = E;
+    g.x0 = x0; g.y0 = y0; g.z0 = z0;
+    g.hx = Lx / nx; g.hy = Ly / ny; g.hz = Lz / nz;
+    g.gamma = gamma;
+    g.J = g.hx * g.hy * g.hz / 8.0;
+    g.hmin = std::fmin(g.hx, std::fmin(g.hy, g.hz));
+    Basis B;
+    make_basis(N, B);
+    for (int a = 0; a < N; ++a) {
+        g.xi[a] = (double)B.x[a];
+        g.w[a] = (double)B.w[a];
+    }
+    const double gf[3] = {2.0 / g.hx, 2.0 / g.hy, 2.0 / g.hz};
+
+    dg::Work w;
+    cudaError_t e = static_scratch_address(&w.face_flux);
+    if (e != cudaSuccess) return DG_ERR_CUDA;
+    if (precision == DG_FP64) {
+        dg::Ops<double> ops;
+        fill_ops(B, gf, ops);
+        e = dg::Launch<double>::rhs(g, ops, (const double *)Q, (double *)R, w, as_stream(stream));
+    } else {
+        dg::Ops<float> ops;
+        fill_ops(B, gf, ops);
+        e = dg::Launch<float>::rhs(g, ops, (const float *)Q, (float *)R, w, as_stream(stream));
+    }
+    return e == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+}
+
 const char *dg_status_string(dg_status s)
 {
     switch (s) {
@@ -315,6 +402,7 @@ const char *dg_status_string(dg_status s)
     case DG_ERR_NONFINITE: return "non-positive or non-finite density or pressure";
     case DG_ERR_BOUNDS: return "index out of bounds";
     case DG_ERR_TIMEOUT: return "timeout";
+    case DG_ERR_TOO_LARGE: return "problem larger than the static scratch of dg_rhs_static";
     }
     return "unknown status";
 }

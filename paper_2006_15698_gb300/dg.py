@@ -62,8 +62,14 @@ _lib.dg_profile_begin.restype = ctypes.c_int
 _lib.dg_profile_end.argtypes = [_vp, _dp, _i64p]
 _lib.dg_profile_end.restype = ctypes.c_int
 
+_lib.dg_rhs_static.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double] * 7 + [
+    ctypes.c_int, _vp, _vp, _vp]
+_lib.dg_rhs_static.restype = ctypes.c_int
+
 DG_PROFILE_KINDS = 5
 KERNEL_KINDS = ("face", "volume", "cfl", "norms", "init")
+DG_ERR_TOO_LARGE = 8
+DG_STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
 class DGError(RuntimeError):
@@ -136,6 +142,14 @@ def dg_status_string(st):
 
 def dg_last_error(h):
     return _lib.dg_last_error(h)
+
+
+def dg_rhs_static(nx, ny, nz, p, x0, y0, z0, Lx, Ly, Lz, gamma, precision, Q, R, stream=None):
+    """Allocation-free right-hand side (no mesh handle; scratch in a static
+    device array, see include/dg.h).  For callers that cannot let a library
+    allocate device memory."""
+    _check(_lib.dg_rhs_static(nx, ny, nz, p, x0, y0, z0, Lx, Ly, Lz, gamma, precision,
+                              _ptr(Q), _ptr(R), _stream(stream)), "dg_rhs_static")
 
 
 def dg_profile_begin(h):
