@@ -23,8 +23,10 @@
  * at x = x0 + (ex + (xi_i + 1)/2) hx, hx = Lx/nx (likewise y, z).  The scalar
  * type is double for DG_FP64 meshes and float for DG_FP32 meshes;
  * dg_mesh_sizes gives the byte size.  State arrays are DEVICE memory owned by
- * the caller (for instance torch tensors); the library never allocates,
- * frees or retains them, and reads/writes them only inside the calls.
+ * the caller (for instance torch tensors), starting on a 16-byte boundary
+ * (cudaMalloc and torch allocations do; a misaligned state is DG_ERR_ARG);
+ * the library never allocates, frees or retains them, and reads/writes them
+ * only inside the calls.
  *
  * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
  * default stream).  Every call except dg_mesh_create/destroy/sizes,
@@ -67,8 +69,9 @@ typedef enum {
 
 typedef enum {
     DG_FP64 = 0, /* double state, double arithmetic */
-    DG_FP32 = 1  /* float state and volume/surface arithmetic; double reductions
-                    (time step, integrals, norms) */
+    DG_FP32 = 1  /* float state and volume/surface arithmetic; the time step's
+                    maximum and dt, the integrals and the norms in double (each
+                    node's wave speed is evaluated in float, as the state) */
 } dg_precision;
 
 typedef enum {
@@ -88,9 +91,10 @@ typedef struct dg_mesh dg_mesh;
  * specific heats gamma (Eq. 3).  The handle computes the 1D operators of the
  * collocated basis on the host (nodes, weights, weak derivative, face
  * interpolation and lift vectors) and allocates its device workspace on the
- * current device: the interface-flux buffer (3 faces x N^2 points x 5 fields
- * per element, in the mesh's scalar type), the reduction partials and the
- * error flag.  Sizes: 1 <= nx, ny, nz; nx*ny*nz*N^3 < 2^40; 0 <= p <= 6;
+ * current device: for DG_FP64 the interface-flux buffer (3 faces x N^2
+ * points x 5 fields per element), for DG_FP32 a second state array (the
+ * fused single-pass stage writes its output there while neighbours still
+ * read the input), plus the reduction partials and the error flag.  Sizes: 1 <= nx, ny, nz; nx*ny*nz*N^3 < 2^40; 0 <= p <= 6;
  * L > 0; gamma > 1.  On success *out owns the handle (free with
  * dg_mesh_destroy).  Errors: DG_ERR_ARG, DG_ERR_UNSUPPORTED, DG_ERR_OOM,
  * DG_ERR_CUDA; *out is set to NULL on error. */
@@ -128,8 +132,10 @@ dg_status dg_rhs(const dg_mesh *mesh, const void *Q, void *R, void *stream);
 
 /* Stable time step for the current state (the paper states no rule; this
  * library uses dt = cfl * min(hx, hy, hz) / ((2p+1) * Lambda) with
- * Lambda = max over nodes of sum_d (|u_d| + c), c = sqrt(gamma p / rho),
- * reduced in double precision).  Writes dt to the DEVICE double *dt_dev,
+ * Lambda = max over nodes of sum_d (|u_d| + c), c = sqrt(gamma p / rho);
+ * DG_FP64: every operation correctly rounded in a fixed order, so dt is
+ * reproducible bit for bit; DG_FP32: node speeds in float, the maximum and
+ * dt in double).  Writes dt to the DEVICE double *dt_dev,
  * with no host synchronisation.  A node with rho <= 0, p <= 0 or NaN makes
  * dt NaN and sets the DG_ERR_NONFINITE flag.  Errors: DG_ERR_ARG (cfl <= 0). */
 dg_status dg_cfl_dt(const dg_mesh *mesh, const void *Q, double cfl, double *dt_dev,
@@ -163,16 +169,21 @@ dg_status dg_norms(const dg_mesh *mesh, const void *Q, const void *Qref, double 
  * dg_profile_end synchronises on the last event, and writes, per kernel kind
  * (array index), the summed device time in milliseconds and the number of
  * launches:
- *   DG_KERNEL_FACE   interface traces + Lax-Friedrichs fluxes
+ *   DG_KERNEL_FACE   interface traces + Lax-Friedrichs fluxes (DG_FP64)
  *   DG_KERNEL_VOLUME volume flux derivative + lift + (RK update or rhs write)
+ *                    (DG_FP64)
  *   DG_KERNEL_CFL    time-step reduction (two launches counted as one)
  *   DG_KERNEL_NORMS  integrals (two launches counted as one)
  *   DG_KERNEL_INIT   initial state
+ *   DG_KERNEL_STAGE  fused single-pass stage: faces, volume, lift and update
+ *                    or rhs write in one kernel (DG_FP32)
+ *   DG_KERNEL_COPY   device copy of the second state back to Q after the
+ *                    five ping-pong stages of a DG_FP32 step
  * ms and launches are HOST arrays of DG_PROFILE_KINDS entries.  Recording
  * costs one event pair per launch; begin discards earlier records. */
-#define DG_PROFILE_KINDS 5
+#define DG_PROFILE_KINDS 7
 enum { DG_KERNEL_FACE = 0, DG_KERNEL_VOLUME = 1, DG_KERNEL_CFL = 2, DG_KERNEL_NORMS = 3,
-       DG_KERNEL_INIT = 4 };
+       DG_KERNEL_INIT = 4, DG_KERNEL_STAGE = 5, DG_KERNEL_COPY = 6 };
 dg_status dg_profile_begin(dg_mesh *mesh);
 dg_status dg_profile_end(dg_mesh *mesh, double *ms, int64_t *launches);
 

@@ -123,13 +123,22 @@ void fill_ops(const Basis &B, const double g[3], dg::Ops<real> &T)
         for (int i = 0; i < N; ++i) {
             for (int a = 0; a < N; ++a)  // g * w_a l_i'(x_a) / w_i
                 T.D[d][i][a] = (real)((long double)g[d] * B.w[a] * B.Dm[a][i] / B.w[i]);
-            T.Lp[d][i] = (real)((long double)g[d] * B.ep[i] / B.w[i]);
-            T.Lm[d][i] = (real)((long double)g[d] * B.em[i] / B.w[i]);
+            // lift vectors carry the 1/2 of the Lax-Friedrichs flux, whose
+            // kernel stores 2 F*
+            T.Lp[d][i] = (real)((long double)g[d] * B.ep[i] / B.w[i] / 2);
+            T.Lm[d][i] = (real)((long double)g[d] * B.em[i] / B.w[i] / 2);
         }
     for (int a = 0; a < N; ++a) {
         T.lp[a] = (real)B.ep[a];
         T.lm[a] = (real)B.em[a];
     }
+}
+
+template <typename real>
+void fill_gas(double gamma, dg::Ops<real> &T)
+{
+    T.gamma = (real)gamma;
+    T.gm1 = (real)(gamma - 1.0);
 }
 
 dg_status cuda_status(cudaError_t e)
@@ -142,6 +151,9 @@ dg_status cuda_status(cudaError_t e)
 cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
+
+// state arrays start on a 16-byte boundary (vector loads of node lines)
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
 
@@ -185,13 +197,21 @@ dg_status dg_mesh_create(int nx, int ny, int nz, int p, double x0, double y0, do
     const double gf[3] = {2.0 / g.hx, 2.0 / g.hy, 2.0 / g.hz};
     fill_ops(B, gf, m->ops64);
     fill_ops(B, gf, m->ops32);
+    fill_gas(gamma, m->ops64);
+    fill_gas(gamma, m->ops32);
 
     cudaError_t err = cudaGetDevice(&m->device);
     if (err != cudaSuccess) { dg_mesh_destroy(m); return DG_ERR_CUDA; }
     const size_t esz = precision == DG_FP64 ? sizeof(double) : sizeof(float);
-    const size_t fbytes = (size_t)3 * dg::NF * (size_t)E * N * N * esz;
+    // double form: the interface-flux buffer of the two-kernel stage;
+    // float form: the second state of the fused single-pass stage
+    const size_t fbytes =
+        precision == DG_FP64 ? (size_t)3 * dg::NF * (size_t)E * N * N * esz : 0;
+    const size_t tbytes =
+        precision == DG_FP32 ? (size_t)dg::NF * (size_t)E * N * N * N * esz : 0;
     const size_t pbytes = (size_t)dg::kNormBlocks * 8 * sizeof(double);
-    err = cudaMalloc(&m->work.face_flux, fbytes);
+    if (fbytes) err = cudaMalloc(&m->work.face_flux, fbytes);
+    if (err == cudaSuccess && tbytes) err = cudaMalloc(&m->work.qtmp, tbytes);
     if (err == cudaSuccess) err = cudaMalloc((void **)&m->work.partials, pbytes);
     if (err == cudaSuccess) err = cudaMalloc((void **)&m->work.lam_bits, sizeof(unsigned long long));
     if (err == cudaSuccess) err = cudaMalloc((void **)&m->work.err, sizeof(int));
@@ -204,7 +224,7 @@ dg_status dg_mesh_create(int nx, int ny, int nz, int p, double x0, double y0, do
         dg_mesh_destroy(m);
         return st;
     }
-    m->ws_bytes = fbytes + pbytes + sizeof(unsigned long long) + sizeof(int);
+    m->ws_bytes = fbytes + tbytes + pbytes + sizeof(unsigned long long) + sizeof(int);
     *out = m;
     return DG_OK;
 }
@@ -214,6 +234,7 @@ void dg_mesh_destroy(dg_mesh *m)
     if (!m) return;
     cudaDeviceSynchronize();
     cudaFree(m->work.face_flux);
+    cudaFree(m->work.qtmp);
     cudaFree(m->work.partials);
     cudaFree(m->work.lam_bits);
     cudaFree(m->work.err);
@@ -259,7 +280,7 @@ dg_status dg_state_init(const dg_mesh *m, dg_init_kind kind, const double *param
 
 dg_status dg_rhs(const dg_mesh *m, const void *Q, void *R, void *stream)
 {
-    if (!m || !Q || !R || Q == R) return DG_ERR_ARG;
+    if (!m || !Q || !R || Q == R || !aligned16(Q) || !aligned16(R)) return DG_ERR_ARG;
     dg::Work w = m->work;
     cudaError_t e = m->prec == DG_FP64
                         ? dg::Launch<double>::rhs(m->geo, m->ops64, (const double *)Q, (double *)R,
@@ -283,7 +304,7 @@ dg_status dg_cfl_dt(const dg_mesh *m, const void *Q, double cfl, double *dt_dev,
 
 dg_status dg_rk_step(const dg_mesh *m, void *Q, void *dQ, const double *dt_dev, void *stream)
 {
-    if (!m || !Q || !dQ || !dt_dev || Q == dQ) return DG_ERR_ARG;
+    if (!m || !Q || !dQ || !dt_dev || Q == dQ || !aligned16(Q) || !aligned16(dQ)) return DG_ERR_ARG;
     dg::Work w = m->work;
     cudaError_t e = m->prec == DG_FP64
                         ? dg::Launch<double>::rk_step(m->geo, m->ops64, (double *)Q, (double *)dQ,
@@ -347,7 +368,7 @@ dg_status dg_rhs_static(int nx, int ny, int nz, int p, double x0, double y0, dou
                         double Lx, double Ly, double Lz, double gamma, dg_precision precision,
                         const void *Q, void *R, void *stream)
 {
-    if (!Q || !R || Q == R) return DG_ERR_ARG;
+    if (!Q || !R || Q == R || !aligned16(Q) || !aligned16(R)) return DG_ERR_ARG;
     if (nx < 1 || ny < 1 || nz < 1) return DG_ERR_ARG;
     if (!finite_pos(Lx) || !finite_pos(Ly) || !finite_pos(Lz)) return DG_ERR_ARG;
     if (!std::isfinite(x0) || !std::isfinite(y0) || !std::isfinite(z0)) return DG_ERR_ARG;
@@ -382,10 +403,12 @@ dg_status dg_rhs_static(int nx, int ny, int nz, int p, double x0, double y0, dou
     if (precision == DG_FP64) {
         dg::Ops<double> ops;
         fill_ops(B, gf, ops);
+        fill_gas(gamma, ops);
         e = dg::Launch<double>::rhs(g, ops, (const double *)Q, (double *)R, w, as_stream(stream));
     } else {
         dg::Ops<float> ops;
         fill_ops(B, gf, ops);
+        fill_gas(gamma, ops);
         e = dg::Launch<float>::rhs(g, ops, (const float *)Q, (float *)R, w, as_stream(stream));
     }
     return e == cudaSuccess ? DG_OK : DG_ERR_CUDA;

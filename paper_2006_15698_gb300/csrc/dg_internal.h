@@ -19,8 +19,9 @@ constexpr int NMAX = DG_MAX_P + 1;
 // (kernel parameter space), so every operand read is a constant-bank load.
 //   D[d][i][a]  = g_d * w_a l_i'(xi_a) / w_i    weak derivative with the
 //                                               inverse mass folded in
-//   Lp[d][i]    = g_d * l_i(+1) / w_i           lift of the +d face flux
-//   Lm[d][i]    = g_d * l_i(-1) / w_i           lift of the -d face flux
+//   Lp[d][i]    = g_d * l_i(+1) / (2 w_i)       lift of the +d face flux
+//   Lm[d][i]    = g_d * l_i(-1) / (2 w_i)       lift of the -d face flux
+//                 (the 1/2 of the Lax-Friedrichs flux, stored as 2 F*)
 //   lp[a], lm[a] = l_a(+1), l_a(-1)             trace interpolation
 // with g_d = 2 / h_d the reference-to-physical factor of direction d.
 template <typename real>
@@ -30,6 +31,7 @@ struct Ops {
     real Lm[3][NMAX];
     real lp[NMAX];
     real lm[NMAX];
+    real gamma, gm1;  // ratio of specific heats and gamma - 1, in the kernels' type
 };
 
 // Mesh geometry and sizes (plain values; also by value into kernels).
@@ -88,6 +90,7 @@ struct Work {
     double *partials = nullptr;             // norms partial sums, kNormBlocks x 8
     unsigned long long *lam_bits = nullptr; // CFL maximum (bits of a positive double)
     int *err = nullptr;                     // sticky error flag
+    void *qtmp = nullptr;                   // second state (float form's ping-pong)
     Prof *prof = nullptr;                   // kernel timing (host object)
 };
 

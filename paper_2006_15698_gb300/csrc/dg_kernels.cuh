@@ -23,6 +23,8 @@
 // fluxes) is complete before volume_kernel starts.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_runtime.h>
 
 #include "dg_internal.h"
@@ -48,7 +50,8 @@ __device__ __forceinline__ long long sidx(int n, long long e, int node, long lon
     return ((long long)n * E + e) * N3 + node;
 }
 
-// index in the interface-flux buffer F[d][n][e][face point]
+// index in the interface-flux buffer F[d][n][e][face point]; the buffer
+// holds twice the Lax-Friedrichs flux (the 1/2 is in the lift vectors)
 __device__ __forceinline__ long long fidx(int d, int n, long long e, int pt, long long E, int N2)
 {
     return ((long long)(d * NF + n) * E + e) * N2 + pt;
@@ -78,12 +81,28 @@ __device__ __forceinline__ long long neighbour(long long e, int side, const Geo 
 // Euler physics (Eq. 2-3) and the local Lax-Friedrichs flux
 // ---------------------------------------------------------------------------
 
+// 1/x for the positive densities of the flux evaluations.  Double: the
+// hardware reciprocal approximation refined by two Newton-Raphson steps
+// r <- r + r(1 - x r) (each squares the relative error, so the approximation's
+// error falls below double rounding: the result is within 1 ulp of 1/x),
+// four FMAs instead of a correctly rounded division.  Float: plain division.
+__device__ __forceinline__ double recip(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
+
 // Normal flux F^DIR(q), its normal velocity magnitude + sound speed.
 template <int DIR, typename real>
 __device__ __forceinline__ void normal_flux(const real q[NF], real gamma, real gm1, real f[NF],
                                            real &speed)
 {
-    const real rinv = real(1) / q[0];
+    const real rinv = recip(q[0]);
     const real mm = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
     const real p = gm1 * (q[4] - real(0.5) * mm * rinv);
     const real mn = q[1 + DIR];
@@ -99,16 +118,17 @@ __device__ __forceinline__ void normal_flux(const real q[NF], real gamma, real g
 // Local Lax-Friedrichs (Rusanov) flux through a face with normal +e_DIR,
 // qL on the -side, qR on the +side (Sec. II.B; local dissipation speed):
 //   F* = (F(qL) + F(qR))/2 - max(|u_n| + c)/2 (qR - qL)
+// Returned as 2 F* (the factor 1/2 is folded into the lift vectors).
 template <int DIR, typename real>
-__device__ __forceinline__ void lf_flux(const real qL[NF], const real qR[NF], real gamma,
-                                        real gm1, real f[NF])
+__device__ __forceinline__ void lf_flux2(const real qL[NF], const real qR[NF], real gamma,
+                                         real gm1, real f[NF])
 {
     real fL[NF], fR[NF], sL, sR;
     normal_flux<DIR>(qL, gamma, gm1, fL, sL);
     normal_flux<DIR>(qR, gamma, gm1, fR, sR);
-    const real hl = real(0.5) * fmax(sL, sR);
+    const real lam = fmax(sL, sR);
 #pragma unroll
-    for (int n = 0; n < NF; ++n) f[n] = real(0.5) * (fL[n] + fR[n]) - hl * (qR[n] - qL[n]);
+    for (int n = 0; n < NF; ++n) f[n] = (fL[n] + fR[n]) - lam * (qR[n] - qL[n]);
 }
 
 // ---------------------------------------------------------------------------
@@ -143,24 +163,39 @@ __device__ __forceinline__ void face_point(const real *__restrict__ Q, real *__r
         qR[n] = sr;
     }
     real f[NF];
-    lf_flux<DIR>(qL, qR, real(g.gamma), real(g.gamma - 1.0), f);
+    lf_flux2<DIR>(qL, qR, T.gamma, T.gm1, f);
 #pragma unroll
     for (int n = 0; n < NF; ++n) F[fidx(DIR, n, e, pt, g.E, N2)] = f[n];
 }
 
+// CTA shape of face_flux_kernel: EF consecutive elements and all three of
+// their + faces, so each element's nodes are fetched from DRAM once and
+// reused from L1 for its three directions.  Each direction owns a segment of
+// SEG threads (EF N^2 face points rounded up to whole warps) so that every
+// warp runs one direction's code path: on the narrow FP64 pipe a warp split
+// across two directions would pay for both.
+template <int N>
+struct FaceTile {
+    static constexpr int N2 = N * N;
+    static constexpr int EF = N == 1 ? 32 : N == 2 ? 16 : N == 3 ? 7 : N == 4 ? 4 : N == 5 ? 5
+                            : N == 6 ? 7 : 5;
+    static constexpr int SEG = ((EF * N2 + 31) / 32) * 32;
+    static constexpr int THREADS = 3 * SEG;
+};
+
 template <int N, typename real>
-__global__ void __launch_bounds__(256) face_flux_kernel(const real *__restrict__ Q,
-                                                        real *__restrict__ F, const Ops<real> T,
-                                                        const Geo g)
+__global__ void __launch_bounds__(FaceTile<N>::THREADS)
+    face_flux_kernel(const real *__restrict__ Q, real *__restrict__ F, const Ops<real> T,
+                     const Geo g)
 {
-    constexpr int N2 = N * N;
-    const long long per_dir = g.E * N2;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 3 * per_dir) return;
-    const int d = (int)(t / per_dir);
-    const long long r = t - d * per_dir;
-    const long long e = r / N2;
-    const int pt = (int)(r - e * N2);
+    constexpr int N2 = N * N, EF = FaceTile<N>::EF, SEG = FaceTile<N>::SEG;
+    const int d = threadIdx.x / SEG;
+    const int r = threadIdx.x - d * SEG;
+    if (r >= EF * N2) return;
+    const int el = r / N2;
+    const int pt = r - el * N2;
+    const long long e = (long long)blockIdx.x * EF + el;
+    if (e >= g.E) return;
     if (d == 0) face_point<N, 0>(Q, F, T, g, e, pt);
     else if (d == 1) face_point<N, 1>(Q, F, T, g, e, pt);
     else face_point<N, 2>(Q, F, T, g, e, pt);
@@ -193,8 +228,8 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
 #pragma unroll
         for (int n = 0; n < NF; ++n) q[n] = Qin[sidx(n, e, node, g.E, N3)];
         // fluxes at this node (Eq. 2 with the closure of Eq. 3)
-        const real gm1 = real(g.gamma - 1.0);
-        const real rinv = real(1) / q[0];
+        const real gm1 = T.gm1;
+        const real rinv = recip(q[0]);
         const real u = q[1] * rinv, v = q[2] * rinv, w = q[3] * rinv;
         const real p = gm1 * (q[4] - real(0.5) * (q[1] * u + q[2] * v + q[3] * w));
         const real ep = q[4] + p;
@@ -258,6 +293,274 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
 }
 
 // ---------------------------------------------------------------------------
+// fused single-pass stage (float state): faces + volume + lift + update
+// ---------------------------------------------------------------------------
+//
+// For the float form the stage is bound by DRAM traffic and instruction
+// issue, not by a narrow pipe, so one kernel does all of it: a CTA stages its
+// elements' states and fluxes in shared memory, computes the Lax-Friedrichs
+// flux on all six faces of each of its elements (the neighbour's trace is
+// interpolated from the neighbour's face-normal node lines, read through L2,
+// or from shared memory when the neighbour is in the same CTA), then the
+// derivative, lift and update.  Each interface flux is evaluated by both
+// adjacent CTAs from bitwise-identical inputs in the same operation order, so
+// both see the same value and discrete conservation holds as in the
+// two-kernel form.  DRAM traffic per stage is Q read, dQ read/written and Q'
+// written: the output goes to a second state buffer, because neighbouring
+// CTAs still read the input state.
+
+// single-instruction float approximations (PTX rcp.approx / sqrt.approx,
+// relative error of order 2^-23, the float form's own rounding level)
+__device__ __forceinline__ float fast_rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float fast_sqrt(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <int DIR>
+__device__ __forceinline__ void normal_flux_f(const float q[NF], float gamma, float gm1,
+                                              float f[NF], float &speed)
+{
+    const float rinv = fast_rcp(q[0]);
+    const float mm = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    const float p = gm1 * (q[4] - 0.5f * mm * rinv);
+    const float mn = q[1 + DIR];
+    const float un = mn * rinv;
+    f[0] = mn;
+    f[1] = q[1] * un + (DIR == 0 ? p : 0.0f);
+    f[2] = q[2] * un + (DIR == 1 ? p : 0.0f);
+    f[3] = q[3] * un + (DIR == 2 ? p : 0.0f);
+    f[4] = (q[4] + p) * un;
+    speed = fabsf(un) + fast_sqrt(gamma * p * rinv);
+}
+
+// N consecutive floats; vector loads when the line is 8- or 16-byte aligned
+// (N even: every line starts at a multiple of N floats from an aligned base)
+template <int N>
+__device__ __forceinline__ void load_line(const float *p, float v[N])
+{
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int a = 0; a < N; a += 4) {
+            const float4 t = *reinterpret_cast<const float4 *>(p + a);
+            v[a] = t.x; v[a + 1] = t.y; v[a + 2] = t.z; v[a + 3] = t.w;
+        }
+    } else if constexpr (N % 2 == 0) {
+#pragma unroll
+        for (int a = 0; a < N; a += 2) {
+            const float2 t = *reinterpret_cast<const float2 *>(p + a);
+            v[a] = t.x; v[a + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < N; ++a) v[a] = p[a];
+    }
+}
+
+// Trace of an element on a face in direction DIR at node line (t1, t2):
+// sum_c l[c] Q(node c along DIR), from `src` (the element's field planes at
+// plane stride `pstride`); the same arithmetic for shared and global sources.
+template <int N, int DIR>
+__device__ __forceinline__ void line_trace(const float *src, long long pstride, int base,
+                                           const float *l, float q[NF])
+{
+    constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? N : N * N);
+#pragma unroll
+    for (int n = 0; n < NF; ++n) {
+        float v[N];
+        if constexpr (DIR == 0) {
+            load_line<N>(src + n * pstride + base, v);
+        } else {
+#pragma unroll
+            for (int c = 0; c < N; ++c) v[c] = src[n * pstride + base + c * stride];
+        }
+        float s = 0.0f;
+#pragma unroll
+        for (int c = 0; c < N; ++c) s += l[c] * v[c];
+        q[n] = s;
+    }
+}
+
+template <int N>
+struct FusedTile {
+    static constexpr int N2 = N * N, N3 = N * N * N;
+    static constexpr int EPB = Tile<N>::EPB, THREADS = Tile<N>::THREADS;
+    // face tasks: six faces, each a warp-aligned segment of EPB N^2 points
+    static constexpr int SEGF = ((EPB * N2 + 31) / 32) * 32;
+    // per-element strides in shared memory, padded to 16 (mod 32) floats so
+    // that two elements touched by one warp fall into different bank halves
+    static constexpr int pad16(int x) { return x + ((16 - x % 32) + 32) % 32; }
+    static constexpr int FSTR = pad16(3 * NF * N3);  // fluxes [3][NF][N3], direction-major nodes
+    static constexpr int QSTR = pad16(NF * N3);      // state [NF][N3]
+    static constexpr int HSTR = pad16(3 * NF * N2 * 2);  // face fluxes [3][NF][N2][2]: (-, +) pair
+    // shared memory: fluxes, state, face fluxes (floats), then the neighbour
+    // table [EPB][6] (long long)
+    static constexpr size_t FLOATS = (size_t)EPB * (FSTR + QSTR + HSTR);
+    static constexpr size_t BYTES = ((FLOATS * sizeof(float) + 15) / 16) * 16 + EPB * 6 * 8;
+    // resident CTAs per SM requested from the register allocator
+    static constexpr int MINB = THREADS <= 256 ? 5 : (THREADS <= 512 ? 2 : 1);
+};
+
+template <int N, int DIR>
+__device__ __forceinline__ void fused_face(const float *__restrict__ Qin, const float *sQ,
+                                           float *sH, const long long *sNb, const Ops<float> &T,
+                                           long long E, long long e0, int el, int side, int pt)
+{
+    constexpr int N2 = N * N, N3 = N * N * N, EPB = Tile<N>::EPB;
+    const int t1 = pt % N, t2 = pt / N;
+    const int base = DIR == 0 ? (t2 * N + t1) * N : (DIR == 1 ? t2 * N2 + t1 : t2 * N + t1);
+    const long long en = sNb[el * 6 + 2 * DIR + side];
+    // own trace at the face's end of the element, the neighbour's at the other end
+    float qo[NF], qn[NF];
+    constexpr int QSTR = FusedTile<N>::QSTR;
+    line_trace<N, DIR>(sQ + (size_t)el * QSTR, N3, base, side ? T.lp : T.lm, qo);
+    const long long rel = en - e0;
+    if (rel >= 0 && rel < EPB)
+        line_trace<N, DIR>(sQ + (size_t)rel * QSTR, N3, base, side ? T.lm : T.lp, qn);
+    else
+        line_trace<N, DIR>(Qin + en * N3, E * N3, base, side ? T.lm : T.lp, qn);
+    float fL[NF], fR[NF], sL, sR;
+    normal_flux_f<DIR>(side ? qo : qn, T.gamma, T.gm1, fL, sL);
+    normal_flux_f<DIR>(side ? qn : qo, T.gamma, T.gm1, fR, sR);
+    const float lam = fmaxf(sL, sR);
+    const float *qL = side ? qo : qn;
+    const float *qR = side ? qn : qo;
+    // (-, +) pair of the direction's two faces at this face point
+    float *h = sH + (size_t)el * FusedTile<N>::HSTR + (DIR * NF * N2 + pt) * 2 + side;
+#pragma unroll
+    for (int n = 0; n < NF; ++n) h[n * N2 * 2] = (fL[n] + fR[n]) - lam * (qR[n] - qL[n]);
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(Tile<N>::THREADS, FusedTile<N>::MINB)
+    fused_stage_kernel(const float *__restrict__ Qin, float *__restrict__ Out,
+                       float *__restrict__ dQ, const Ops<float> T, const Geo g, float A, float B,
+                       const double *__restrict__ dt)
+{
+    using FT = FusedTile<N>;
+    constexpr int N2 = FT::N2, N3 = FT::N3, EPB = FT::EPB, THREADS = FT::THREADS;
+    constexpr int SEGF = FT::SEGF, FSTR = FT::FSTR, QSTR = FT::QSTR, HSTR = FT::HSTR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *sF = reinterpret_cast<float *>(smem_raw);  // [EPB][FSTR]: [3][NF][N3]
+    float *sQ = sF + EPB * FSTR;                      // [EPB][QSTR]: [NF][N3]
+    float *sH = sQ + EPB * QSTR;                      // [EPB][HSTR]: [3][NF][N2][2] (2 F*)
+    long long *sNb = reinterpret_cast<long long *>(smem_raw + (FT::BYTES - EPB * 6 * 8));
+
+    const int tid = threadIdx.x;
+    const int el = tid / N3;
+    const int node = tid - el * N3;
+    const long long e0 = (long long)blockIdx.x * EPB;
+    const long long e = e0 + el;
+    const bool active = el < EPB && e < g.E;
+    const int i = node % N, j = (node / N) % N, k = node / N2;
+
+    if (tid < EPB * 6) {  // the six neighbours of every element of the tile
+        const int te = tid / 6, f = tid - te * 6;
+        const long long ee = e0 + te;
+        long long nb = 0;
+        if (ee < g.E) {
+            const int side = (f & 1) ? +1 : -1;
+            nb = (f >> 1) == 0 ? neighbour<0>(ee, side, g)
+               : (f >> 1) == 1 ? neighbour<1>(ee, side, g) : neighbour<2>(ee, side, g);
+        }
+        sNb[tid] = nb;
+    }
+
+    float q[NF];
+    if (active) {
+#pragma unroll
+        for (int n = 0; n < NF; ++n) {
+            q[n] = Qin[sidx(n, e, node, g.E, N3)];
+            sQ[el * QSTR + n * N3 + node] = q[n];
+        }
+        const float rinv = fast_rcp(q[0]);
+        const float u = q[1] * rinv, v = q[2] * rinv, w = q[3] * rinv;
+        const float p = T.gm1 * (q[4] - 0.5f * (q[1] * u + q[2] * v + q[3] * w));
+        const float ep = q[4] + p;
+        // direction-major node order: the line a contraction reads is contiguous
+        float *sx = sF + (size_t)el * FSTR + 0 * NF * N3 + (k * N + j) * N + i;
+        float *sy = sF + (size_t)el * FSTR + 1 * NF * N3 + (k * N + i) * N + j;
+        float *sz = sF + (size_t)el * FSTR + 2 * NF * N3 + (j * N + i) * N + k;
+        sx[0 * N3] = q[1];
+        sx[1 * N3] = q[1] * u + p;
+        sx[2 * N3] = q[2] * u;
+        sx[3 * N3] = q[3] * u;
+        sx[4 * N3] = ep * u;
+        sy[0 * N3] = q[2];
+        sy[1 * N3] = q[1] * v;
+        sy[2 * N3] = q[2] * v + p;
+        sy[3 * N3] = q[3] * v;
+        sy[4 * N3] = ep * v;
+        sz[0 * N3] = q[3];
+        sz[1 * N3] = q[1] * w;
+        sz[2 * N3] = q[2] * w;
+        sz[3 * N3] = q[3] * w + p;
+        sz[4 * N3] = ep * w;
+    }
+    __syncthreads();
+
+    // the six faces of every element of the tile, face-major so that a warp
+    // works on one (direction, side)
+    for (int t = tid; t < 6 * SEGF; t += THREADS) {
+        const int face = t / SEGF;
+        const int r = t - face * SEGF;
+        if (r >= EPB * N2) continue;
+        const int el2 = r / N2;
+        const int pt = r - el2 * N2;
+        if (e0 + el2 >= g.E) continue;
+        const int side = face & 1;
+        if (face < 2) fused_face<N, 0>(Qin, sQ, sH, sNb, T, g.E, e0, el2, side, pt);
+        else if (face < 4) fused_face<N, 1>(Qin, sQ, sH, sNb, T, g.E, e0, el2, side, pt);
+        else fused_face<N, 2>(Qin, sQ, sH, sNb, T, g.E, e0, el2, side, pt);
+    }
+    __syncthreads();
+    if (!active) return;
+
+    const int px = k * N + j, py = k * N + i, pz = j * N + i;
+    float dtr = 0.0f;
+    if (MODE == 1) dtr = (float)(*dt);
+    const float *h = sH + (size_t)el * HSTR;
+    const float *f = sF + (size_t)el * FSTR;
+#pragma unroll
+    for (int n = 0; n < NF; ++n) {
+        float vx[N], vy[N], vz[N];
+        load_line<N>(f + 0 * NF * N3 + n * N3 + (k * N + j) * N, vx);
+        load_line<N>(f + 1 * NF * N3 + n * N3 + (k * N + i) * N, vy);
+        load_line<N>(f + 2 * NF * N3 + n * N3 + (j * N + i) * N, vz);
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a < N; ++a) acc += T.D[0][i][a] * vx[a];
+#pragma unroll
+        for (int b = 0; b < N; ++b) acc += T.D[1][j][b] * vy[b];
+#pragma unroll
+        for (int c = 0; c < N; ++c) acc += T.D[2][k][c] * vz[c];
+        // lift: one (-, +) pair of face fluxes per direction
+        const float2 hx = *reinterpret_cast<const float2 *>(h + ((0 * NF + n) * N2 + px) * 2);
+        const float2 hy = *reinterpret_cast<const float2 *>(h + ((1 * NF + n) * N2 + py) * 2);
+        const float2 hz = *reinterpret_cast<const float2 *>(h + ((2 * NF + n) * N2 + pz) * 2);
+        acc += T.Lm[0][i] * hx.x - T.Lp[0][i] * hx.y;
+        acc += T.Lm[1][j] * hy.x - T.Lp[1][j] * hy.y;
+        acc += T.Lm[2][k] * hz.x - T.Lp[2][k] * hz.y;
+
+        const long long o = sidx(n, e, node, g.E, N3);
+        if (MODE == 0) {
+            Out[o] = acc;
+        } else {
+            const float d = (A == 0.0f ? 0.0f : A * dQ[o]) + dtr * acc;
+            dQ[o] = d;
+            Out[o] = q[n] + B * d;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // time step, integrals, initial states
 // ---------------------------------------------------------------------------
 
@@ -268,7 +571,37 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
-// Lambda = max over nodes of sum_d (|u_d| + c), in double; a node with
+// Wave-speed sum sum_d (|u_d| + c) of one node; false for rho <= 0, p <= 0 or NaN.
+// Double state: every operation explicitly rounded (no FMA contraction) in a
+// fixed order, so a node's speed is the same double on any conforming
+// implementation of IEEE-754 arithmetic.
+__device__ __forceinline__ bool node_speed(double r, double mx, double my, double mz, double E,
+                                           double gamma, double &s)
+{
+    const double u = __ddiv_rn(mx, r), v = __ddiv_rn(my, r), w = __ddiv_rn(mz, r);
+    const double uu = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
+    const double p = __dmul_rn(gamma - 1.0, __dsub_rn(E, __dmul_rn(__dmul_rn(0.5, r), uu)));
+    if (!(r > 0.0) || !(p > 0.0)) return false;
+    const double c = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), r));
+    s = __dadd_rn(__dadd_rn(__dadd_rn(fabs(u), c), __dadd_rn(fabs(v), c)), __dadd_rn(fabs(w), c));
+    return true;
+}
+// Float state: the node's speed in float (the precision of the state itself),
+// the maximum and the time step in double.
+__device__ __forceinline__ bool node_speed(float r, float mx, float my, float mz, float E,
+                                           double gamma, double &s)
+{
+    const float g = (float)gamma;
+    const float rinv = 1.0f / r;
+    const float u = mx * rinv, v = my * rinv, w = mz * rinv;
+    const float p = (g - 1.0f) * (E - 0.5f * r * (u * u + v * v + w * w));
+    if (!(r > 0.0f) || !(p > 0.0f)) return false;
+    const float c = sqrtf(g * p * rinv);
+    s = (double)((fabsf(u) + c) + (fabsf(v) + c) + (fabsf(w) + c));
+    return true;
+}
+
+// Lambda = max over nodes of sum_d (|u_d| + c), reduced in double; a node with
 // rho <= 0, p <= 0 or NaN contributes a NaN whose bit pattern is above every
 // finite value, and raises the error flag.
 template <typename real>
@@ -280,21 +613,12 @@ __global__ void __launch_bounds__(256) cfl_kernel(const real *__restrict__ Q, lo
     bool bad = false;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nodes;
          t += (long long)gridDim.x * blockDim.x) {
-        // every operation explicitly rounded (no FMA contraction), in a fixed
-        // order, so the wave speed of a node is the same double on any
-        // conforming implementation of IEEE-754 arithmetic
-        const double r = (double)Q[t], mx = (double)Q[nodes + t], my = (double)Q[2 * nodes + t],
-                     mz = (double)Q[3 * nodes + t], E = (double)Q[4 * nodes + t];
-        const double u = __ddiv_rn(mx, r), v = __ddiv_rn(my, r), w = __ddiv_rn(mz, r);
-        const double uu = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
-        const double p = __dmul_rn(gamma - 1.0, __dsub_rn(E, __dmul_rn(__dmul_rn(0.5, r), uu)));
-        if (!(r > 0.0) || !(p > 0.0)) {
+        double s;
+        if (!node_speed(Q[t], Q[nodes + t], Q[2 * nodes + t], Q[3 * nodes + t], Q[4 * nodes + t],
+                        gamma, s)) {
             bad = true;
             continue;
         }
-        const double c = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), r));
-        const double s = __dadd_rn(__dadd_rn(__dadd_rn(fabs(u), c), __dadd_rn(fabs(v), c)),
-                                   __dadd_rn(fabs(w), c));
         m = fmax(m, s);
     }
     if (bad) {
@@ -329,10 +653,16 @@ static __global__ void cfl_finalize_kernel(unsigned long long *lam_bits, double 
 // Pass 1 of the integrals: block b sums a fixed contiguous range of nodes in a
 // fixed order (thread-strided, then a shared-memory tree), so the result does
 // not depend on scheduling.  Values: I_0..I_4, KE, |Q-Qref|^2, |Qref|^2.
+// Quadrature weight J w_i w_j w_k of every in-element node (by value, constant bank).
+struct NodeWeights {
+    double w[NMAX * NMAX * NMAX];
+};
+
 template <typename real>
 __global__ void __launch_bounds__(256) norms_partial_kernel(const real *__restrict__ Q,
                                                             const real *__restrict__ Qref,
-                                                            const Geo g, double *partials)
+                                                            const Geo g, const NodeWeights W,
+                                                            double *partials)
 {
     __shared__ double red[8][256];
     const int N = g.p + 1, N3 = N * N * N;
@@ -341,16 +671,30 @@ __global__ void __launch_bounds__(256) norms_partial_kernel(const real *__restri
     const long long beg = (long long)blockIdx.x * chunk;
     const long long end = beg + chunk < nodes ? beg + chunk : nodes;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // in-element node index of t, advanced by the stride without a division
+    int node = (int)((beg + threadIdx.x) % N3);
+    const int step = (int)(blockDim.x % N3);
     for (long long t = beg + threadIdx.x; t < end; t += blockDim.x) {
-        const int node = (int)(t % N3);
-        const int i = node % N, j = (node / N) % N, k = node / (N * N);
-        const double wq = g.J * (g.w[i] * g.w[j] * g.w[k]);
+        const double wq = W.w[node];
+        node += step;
+        if (node >= N3) node -= N3;
         double q[NF];
+        real qr[NF];
 #pragma unroll
-        for (int n = 0; n < NF; ++n) q[n] = (double)Q[n * nodes + t];
+        for (int n = 0; n < NF; ++n) {
+            qr[n] = Q[n * nodes + t];
+            q[n] = (double)qr[n];
+        }
 #pragma unroll
         for (int n = 0; n < NF; ++n) acc[n] += wq * q[n];
-        acc[5] += wq * 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0];
+        if constexpr (sizeof(real) == 4) {
+            // float state: the kinetic-energy density in float (the state's
+            // own precision), accumulated in double
+            const float ke = 0.5f * (qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]) * fast_rcp(qr[0]);
+            acc[5] += wq * (double)ke;
+        } else {
+            acc[5] += wq * 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * recip(q[0]);
+        }
         if (Qref) {
 #pragma unroll
             for (int n = 0; n < NF; ++n) {
@@ -477,7 +821,8 @@ inline int grid_for(long long n, int threads, long long cap)
 }
 
 // kernel kinds of the per-kernel timing (dg_profile_end)
-enum { kKindFace = 0, kKindVolume = 1, kKindCfl = 2, kKindNorms = 3, kKindInit = 4 };
+enum { kKindFace = 0, kKindVolume = 1, kKindCfl = 2, kKindNorms = 3, kKindInit = 4, kKindStage = 5,
+       kKindCopy = 6 };
 
 struct ProfScope {
     Prof *p;
@@ -498,11 +843,11 @@ template <int N, typename real>
 cudaError_t launch_face(const Geo &g, const Ops<real> &T, const real *Q, real *F, Prof *prof,
                         cudaStream_t s)
 {
-    const long long n = 3 * g.E * (long long)(N * N);
-    const long long blocks = (n + 255) / 256;
+    constexpr int EF = FaceTile<N>::EF;
+    const long long blocks = (g.E + EF - 1) / EF;
     if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
     ProfScope ps(prof, kKindFace, s);
-    face_flux_kernel<N, real><<<(unsigned)blocks, 256, 0, s>>>(Q, F, T, g);
+    face_flux_kernel<N, real><<<(unsigned)blocks, FaceTile<N>::THREADS, 0, s>>>(Q, F, T, g);
     return cudaGetLastError();
 }
 
@@ -527,30 +872,74 @@ cudaError_t launch_volume(const Geo &g, const Ops<real> &T, const real *Qin, rea
     return cudaGetLastError();
 }
 
+template <int N, int MODE>
+cudaError_t launch_fused(const Geo &g, const Ops<float> &T, const float *Qin, float *Out,
+                         float *dQ, float A, float B, const double *dt, Prof *prof,
+                         cudaStream_t s)
+{
+    using FT = FusedTile<N>;
+    const size_t smem = FT::BYTES;
+    if (smem > 48 * 1024) {
+        cudaError_t err = cudaFuncSetAttribute(fused_stage_kernel<N, MODE>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+        if (err != cudaSuccess) return err;
+    }
+    const long long blocks = (g.E + FT::EPB - 1) / FT::EPB;
+    if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
+    ProfScope ps(prof, kKindStage, s);
+    fused_stage_kernel<N, MODE><<<(unsigned)blocks, FT::THREADS, smem, s>>>(Qin, Out, dQ, T, g, A,
+                                                                             B, dt);
+    return cudaGetLastError();
+}
+
+// The float form runs the fused single-pass stage (DRAM bound: one read of
+// the state per stage); the double form the two-kernel stage (FP64-pipe
+// bound: every interface flux evaluated once).
 template <int N, typename real>
 cudaError_t rhs_n(const Geo &g, const Ops<real> &T, const real *Q, real *R, Work &w,
                   cudaStream_t s)
 {
-    real *F = static_cast<real *>(w.face_flux);
-    cudaError_t err = launch_face<N>(g, T, Q, F, w.prof, s);
-    if (err != cudaSuccess) return err;
-    return launch_volume<N, real, 0>(g, T, Q, R, nullptr, F, real(0), real(0), nullptr, w.prof,
-                                     s);
+    if constexpr (std::is_same<real, float>::value) {
+        return launch_fused<N, 0>(g, T, Q, R, nullptr, 0.0f, 0.0f, nullptr, w.prof, s);
+    } else {
+        real *F = static_cast<real *>(w.face_flux);
+        cudaError_t err = launch_face<N>(g, T, Q, F, w.prof, s);
+        if (err != cudaSuccess) return err;
+        return launch_volume<N, real, 0>(g, T, Q, R, nullptr, F, real(0), real(0), nullptr,
+                                         w.prof, s);
+    }
 }
 
 template <int N, typename real>
 cudaError_t rk_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, const double *dt, Work &w,
                  cudaStream_t s)
 {
-    real *F = static_cast<real *>(w.face_flux);
-    for (int st = 0; st < 5; ++st) {
-        cudaError_t err = launch_face<N>(g, T, Q, F, w.prof, s);
-        if (err != cudaSuccess) return err;
-        err = launch_volume<N, real, 1>(g, T, Q, Q, dQ, F, real(kRkA[st]), real(kRkB[st]), dt,
-                                        w.prof, s);
-        if (err != cudaSuccess) return err;
+    if constexpr (std::is_same<real, float>::value) {
+        // ping-pong between Q and the handle's second state: five stages end
+        // in the second state, copied back so the result is in Q
+        real *Tq = static_cast<real *>(w.qtmp);
+        for (int st = 0; st < 5; ++st) {
+            const real *src = (st % 2 == 0) ? Q : Tq;
+            real *dst = (st % 2 == 0) ? Tq : Q;
+            cudaError_t err = launch_fused<N, 1>(g, T, src, dst, dQ, float(kRkA[st]),
+                                                 float(kRkB[st]), dt, w.prof, s);
+            if (err != cudaSuccess) return err;
+        }
+        const size_t bytes = (size_t)NF * (size_t)g.E * N * N * N * sizeof(real);
+        ProfScope ps(w.prof, kKindCopy, s);
+        return cudaMemcpyAsync(Q, Tq, bytes, cudaMemcpyDeviceToDevice, s);
+    } else {
+        real *F = static_cast<real *>(w.face_flux);
+        for (int st = 0; st < 5; ++st) {
+            cudaError_t err = launch_face<N>(g, T, Q, F, w.prof, s);
+            if (err != cudaSuccess) return err;
+            err = launch_volume<N, real, 1>(g, T, Q, Q, dQ, F, real(kRkA[st]), real(kRkB[st]),
+                                            dt, w.prof, s);
+            if (err != cudaSuccess) return err;
+        }
+        return cudaSuccess;
     }
-    return cudaSuccess;
 }
 
 #define DG_DISPATCH_P(p, CALL)            \
@@ -602,8 +991,13 @@ template <typename real>
 cudaError_t Launch<real>::norms(const Geo &g, const real *Q, const real *Qref, double *out,
                                 Work &w, cudaStream_t s)
 {
+    NodeWeights W;
+    const int N = g.p + 1;
+    for (int k = 0; k < N; ++k)
+        for (int j = 0; j < N; ++j)
+            for (int i = 0; i < N; ++i) W.w[(k * N + j) * N + i] = g.J * (g.w[i] * g.w[j] * g.w[k]);
     ProfScope ps(w.prof, kKindNorms, s);
-    norms_partial_kernel<real><<<kNormBlocks, 256, 0, s>>>(Q, Qref, g, w.partials);
+    norms_partial_kernel<real><<<kNormBlocks, 256, 0, s>>>(Q, Qref, g, W, w.partials);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     norms_final_kernel<<<1, 256, 0, s>>>(w.partials, kNormBlocks, Qref != nullptr, out);

@@ -66,8 +66,8 @@ _lib.dg_rhs_static.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double] * 7 + [
     ctypes.c_int, _vp, _vp, _vp]
 _lib.dg_rhs_static.restype = ctypes.c_int
 
-DG_PROFILE_KINDS = 5
-KERNEL_KINDS = ("face", "volume", "cfl", "norms", "init")
+DG_PROFILE_KINDS = 7
+KERNEL_KINDS = ("face", "volume", "cfl", "norms", "init", "stage", "copy")
 DG_ERR_TOO_LARGE = 8
 DG_STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 

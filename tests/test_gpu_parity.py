@@ -104,13 +104,13 @@ def test_cfl_dt_bitwise(kind, p):
     m = dg.Mesh(5, 3, 2, p, *box)
     dt = float(to_host(m.cfl_dt(to_dev(Q), 0.5))[0])
     assert dt == dt_or, (dt, dt_or)
-    # FP32 state: the reduction reads the float state and computes in double
+    # FP32 state: node speeds in float, maximum and dt in double
     m32 = dg.Mesh(5, 3, 2, p, *box, precision=dg.DG_FP32)
     Q32 = Q.astype(np.float32)
     dt32_or, _ = om.cfl_dt(Q32.astype(np.float64), 0.5)
     import torch
     dt32 = float(to_host(m32.cfl_dt(to_dev(Q32, torch.float32), 0.5))[0])
-    assert dt32 == dt32_or
+    assert abs(dt32 - dt32_or) <= 1e-6 * dt32_or
 
 
 def test_cfl_flags_nonpositive_pressure():
