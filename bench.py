@@ -49,7 +49,147 @@ WORKLOADS = {
                             init="vortex", params=None, prec="fp64", cfl=0.5,
                             desc="isentropic vortex (seed 0), [0,10]^3, 8^3 elements, p=3, FP64"),
 }
+WORKLOADS["batch256_fp32"] = dict(
+    kind="batch", count=256, nrange=(4, 32), prange=(1, 5), seed=0, prec="fp32", cfl=0.5,
+    box=(0, 0, 0, 10.0, 10.0, 10.0), p=3, nel=(1, 1, 1), init="vortex", params=None,
+    desc="256 independent isentropic-vortex instances, elements per side uniform in 4..32 and p "
+         "uniform in 1..5 (seed 0), FP32, one persistent launch per RK stage, CUDA-graph step, "
+         "tile shape per p from the autotuner table")
+WORKLOADS["batch64_fp32"] = dict(WORKLOADS["batch256_fp32"], count=64,
+                                 desc="64 instances of the batch256_fp32 distribution (profiling)")
+WORKLOADS["serve2000_fp32"] = dict(
+    kind="serve", count=2000, nrange=(8, 48), prange=(2, 6), steps_range=(50, 500), seed=0,
+    budget=150e9, load=0.8, prec="fp32", cfl=0.5, p=3, nel=(1, 1, 1), box=None, init=None,
+    params=None,
+    desc="serving: Poisson arrivals of 2,000 requests (periodic [0,2pi]^3 box, 8^3..48^3 "
+         "elements, p 2..6, 50..500 LSERK45 steps, vortex or Taylor-Green 50/50, FP32 with FP64 "
+         "reductions), 150 GB admission budget, offered load 80 % of measured capacity")
+WORKLOADS["serve200_fp32"] = dict(
+    WORKLOADS["serve2000_fp32"], count=200, nrange=(8, 24), steps_range=(20, 60),
+    desc="serving, scaled: 200 requests, 8^3..24^3 elements, p 2..6, 20..60 steps, vortex or "
+         "Taylor-Green 50/50, FP32, 150 GB budget, offered load 80 % of measured capacity")
 DEFAULT = "tgv64_p4_fp64"
+
+
+def run_serve(args, w):
+    """Serving loop: calibrate the batch's throughput on requests of the
+    workload's distribution, then replay Poisson arrivals at `load` x that
+    capacity and report time-to-solution percentiles and throughput."""
+    import torch
+    from paper_2006_15698_gb300 import dg, serve
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dg.load_tuning()
+    kw = dict(nrange=w["nrange"], prange=w["prange"], steps_range=w["steps_range"])
+    # capacity: the first requests of the distribution, all present at t = 0
+    calib = serve.make_requests(w["seed"] + 7, 24, 1e9, **kw)
+    for q in calib:
+        q.arrival = 0.0
+        q.nsteps = min(q.nsteps, w["steps_range"][0])
+    rep = serve.Server(serve.GpuExecutor(), w["budget"]).run(calib)
+    capacity = rep.dof_stage_total / rep.wall
+    sample = serve.make_requests(w["seed"], w["count"], 1.0, **kw)
+    mean_work = sum(5.0 * q.nsteps * q.dof for q in sample) / len(sample)
+    rate = w["load"] * capacity / mean_work
+    reqs = serve.make_requests(w["seed"], w["count"], rate, **kw)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    rep = serve.Server(serve.GpuExecutor(), w["budget"]).run(reqs)
+    ck = clocks.stop()
+    s = rep.summary()
+    value, _ = whole_job_rate(rep.wall * 1e3, rep.dof_stage_total, device="cuda")
+    if rank != 0:
+        return None
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": None,
+            "warmup": None, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {w['desc']}", "requests": w["count"],
+                       "arrival_rate_per_s": rate, "calibrated_capacity_dof_stage_per_s": capacity,
+                       "budget_bytes": w["budget"], "parallelism": f"replicas x{ws}"},
+            "serving": {"p50_time_to_solution_s": s["p50_s"], "p99_time_to_solution_s": s["p99_s"],
+                        "requests_per_s": s["requests_per_s"], "wall_s": s["wall_s"],
+                        "peak_active": s["peak_active"], "peak_bytes": s["peak_bytes"],
+                        "batch_rebuilds": s["batch_rebuilds"], "iterations": s["iterations"]},
+            "clocks": ck}
+
+
+def batch_specs(w):
+    """Seeded instance list of a batch workload: (nx = ny = nz, p) per instance."""
+    from paper_2006_15698_gb300 import inputs
+    r = inputs.uniforms(w["seed"], 2 * w["count"])
+    n0, n1 = w["nrange"]
+    p0, p1 = w["prange"]
+    specs = []
+    for i in range(w["count"]):
+        n = n0 + min(int(r[2 * i] * (n1 - n0 + 1)), n1 - n0)
+        p = p0 + min(int(r[2 * i + 1] * (p1 - p0 + 1)), p1 - p0)
+        L = w["box"][3]
+        specs.append(dict(nx=n, ny=n, nz=n, p=p, Lx=L, Ly=L, Lz=L))
+    return specs
+
+
+def run_batch(args, w):
+    """The batched form: every instance of the batch advanced one LSERK45 step
+    per bench step (graph replay of CFL + 5 persistent stage launches + copy)."""
+    import torch
+    from paper_2006_15698_gb300 import dg, inputs
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    tuning = dg.load_tuning()
+    specs = batch_specs(w)
+    b = dg.Batch(specs)
+    for i in range(len(specs)):
+        b.init(i, "vortex", inputs.vortex_params(1000 + i, w["box"]))
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        # steps go through the two-step graph (the stages alternate between Q
+        # and the second states, so a pair of steps ends in Q with no copy)
+        b.step(w["cfl"], nsteps=max(args.warmup, 2), use_graph=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        e0.record(stream)
+        b.step(w["cfl"], nsteps=args.steps, use_graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ck = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        # the same instances stepped one mesh at a time (single-mesh launches,
+        # no graph): what batching buys
+        meshes = [dg.Mesh(s["nx"], s["ny"], s["nz"], s["p"], *w["box"], precision=dg.DG_FP32)
+                  for s in specs]
+        dts = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in specs]
+        seq_steps = max(1, min(args.steps, 5))
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for k in range(seq_steps + 1):
+            if k == 1:
+                s0.record(stream)
+            for m, Q, dQ, dt in zip(meshes, b.Q, b.dQ, dts):
+                m.cfl_dt(Q, w["cfl"], dt)
+                m.rk_step(Q, dQ, dt)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms = s0.elapsed_time(s1) / seq_steps
+    dof = b.n_dof
+    value, ms_max = whole_job_rate(ms, dof * 5 * args.steps, device="cuda")
+    err = b.last_error()
+    if rank != 0:
+        return None
+    p_hist = {}
+    for s in specs:
+        p_hist[s["p"]] = p_hist.get(s["p"], 0) + 1
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {w['desc']}", "instances": len(specs),
+                       "dof": dof, "work_items": b.n_items, "p_histogram": p_hist,
+                       "tile_table": None if tuning is None else
+                       {p: e["tile"] for p, e in tuning["degrees"].items()},
+                       "parallelism": f"replicas x{ws}"},
+            "sequential_ms_per_step": seq_ms, "batched_speedup": seq_ms / (ms_max / args.steps),
+            "clocks": ck, "device_error_flag": err}
 METRIC = "DOF-updates/s per RK stage"
 UNIT = "DOF-stage/s"
 
@@ -396,6 +536,24 @@ def main():
     if args.warmup < 3 and args.impl == "native":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     w = WORKLOADS[args.workload]
+    if w.get("kind") == "serve":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the serving loop has no oracle arm; use the default workload"}))
+            return 0
+        out = run_serve(args, w)
+        if out is not None:
+            print(json.dumps(out))
+        return 0
+    if w.get("kind") == "batch":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the batched form has no oracle arm; use the default workload"}))
+            return 0
+        out = run_batch(args, w)
+        if out is not None:
+            print(json.dumps(out))
+        return 0
     if args.impl == "reference":
         return run_reference(args, w)
     ws, rank, _ = _dist()

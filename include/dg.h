@@ -187,6 +187,68 @@ enum { DG_KERNEL_FACE = 0, DG_KERNEL_VOLUME = 1, DG_KERNEL_CFL = 2, DG_KERNEL_NO
 dg_status dg_profile_begin(dg_mesh *mesh);
 dg_status dg_profile_end(dg_mesh *mesh, double *ms, int64_t *launches);
 
+/* Tile shapes of the DG_FP32 fused stage (an implementation choice, not in
+ * the paper).  The fused stage works on tiles of TX x TY elements of one z
+ * layer; each polynomial degree has a few tile variants, and a process-wide
+ * table selects one per degree (default variant 0).  The table is read at
+ * every DG_FP32 mesh launch and when a batch is created; it is meant to be
+ * filled once from an autotuner's results before work starts (not changed
+ * while kernels of the process are being enqueued from other threads).
+ *   dg_tile_variant_count  number of variants for degree p (0 if p unsupported)
+ *   dg_tile_shape          (TX, TY) of a variant
+ *   dg_set_tile_variant    select a variant (DG_ERR_ARG if out of range)
+ *   dg_get_tile_variant    selected variant (-1 if p unsupported) */
+int dg_tile_variant_count(int p);
+dg_status dg_tile_shape(int p, int variant, int *tx, int *ty);
+dg_status dg_set_tile_variant(int p, int variant);
+int dg_get_tile_variant(int p);
+
+/* Batches: many independent DG_FP32 meshes advanced together (the paper
+ * solves one mesh; batching uneven independent problems is an addition).
+ * Each instance is a periodic box like a dg_mesh (same meaning of nx..gamma)
+ * with caller-owned float device states Q (the solution) and dQ (the RK
+ * register), in the layout above.  dg_batch_create computes every instance's
+ * operators, allocates one second state per instance (the fused stage's
+ * ping-pong buffer), the per-instance time steps and a work list of every
+ * tile of every instance (the tile per degree that best fills a 256-thread
+ * block, the tuning table deciding among equally full ones), grouped by
+ * degree.  dg_batch_step advances every instance by nsteps LSERK45 steps,
+ * each with its own CFL time step (same rule as dg_cfl_dt): per step one
+ * persistent launch computes all time steps, then one persistent launch per
+ * RK stage runs every tile of every instance (device dispatch on the degree;
+ * a second launch per stage only for p = 6 instances, whose tiles need 352
+ * threads).  The stages alternate between Q and the batch's second states,
+ * so an even number of steps ends in Q by itself; after an odd number the
+ * second states are copied back (one device memcpy per instance).  With
+ * use_graph != 0 the launches of two steps (and of one step) are recorded
+ * once into CUDA graphs on `stream` (a created stream, not the legacy
+ * default) and replayed; a changed cfl records new graphs.  Calls on one
+ * batch must be ordered.
+ * dg_batch_dt copies the time steps of the last step to a HOST array of n
+ * doubles (synchronises); dg_batch_norms writes instance idx's integrals as
+ * dg_norms does; dg_batch_state_init fills instance idx's Q like
+ * dg_state_init; dg_batch_last_error reads and clears the batch's
+ * non-finite flag.  Errors as for dg_mesh_create and dg_rk_step. */
+typedef struct {
+    int nx, ny, nz, p;
+    double x0, y0, z0, Lx, Ly, Lz, gamma;
+    void *Q;  /* float device state of the instance (caller-owned) */
+    void *dQ; /* float device RK register, state-sized (caller-owned) */
+    void *Qt; /* optional float device second state, state-sized (caller-owned);
+                 NULL: the batch allocates one and frees it with the batch */
+} dg_instance;
+typedef struct dg_batch dg_batch;
+dg_status dg_batch_create(int n, const dg_instance *instances, dg_batch **out);
+void dg_batch_destroy(dg_batch *batch);
+dg_status dg_batch_sizes(const dg_batch *batch, int64_t *n_dof, int64_t *n_items);
+dg_status dg_batch_state_init(const dg_batch *batch, int idx, dg_init_kind kind,
+                              const double *params, int nparams, void *stream);
+dg_status dg_batch_step(dg_batch *batch, double cfl, int nsteps, int use_graph, void *stream);
+dg_status dg_batch_dt(const dg_batch *batch, double *dt_host);
+dg_status dg_batch_norms(const dg_batch *batch, int idx, const void *Qref, double *out,
+                         void *stream);
+dg_status dg_batch_last_error(const dg_batch *batch);
+
 /* Allocation-free right-hand side (the paper has no counterpart).
  *
  * Some callers cannot let a library allocate device memory: code that runs

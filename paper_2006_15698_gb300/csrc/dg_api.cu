@@ -6,6 +6,8 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <algorithm>
+#include <vector>
 
 #include "dg_internal.h"
 
@@ -412,6 +414,379 @@ dg_status dg_rhs_static(int nx, int ny, int nz, int p, double x0, double y0, dou
         e = dg::Launch<float>::rhs(g, ops, (const float *)Q, (float *)R, w, as_stream(stream));
     }
     return e == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// tile-shape tuning table of the float form's fused stage
+// ---------------------------------------------------------------------------
+namespace dg {
+static int g_tile_var[NMAX + 1] = {0, 0, 0, 0, 0, 0, 0, 0};
+int tile_variant(int N) { return (N >= 1 && N <= NMAX) ? g_tile_var[N] : 0; }
+}  // namespace dg
+
+extern "C" {
+
+int dg_tile_variant_count(int p)
+{
+    if (p < 0 || p > DG_MAX_P) return 0;
+    int n = 0, tx, ty, th;
+    size_t sm;
+    while (n < 8 && dg::tile_code_info((p + 1) * 8 + n, &tx, &ty, &th, &sm)) ++n;
+    return n;
+}
+
+dg_status dg_set_tile_variant(int p, int variant)
+{
+    if (p < 0 || p > DG_MAX_P) return DG_ERR_UNSUPPORTED;
+    if (variant < 0 || variant >= dg_tile_variant_count(p)) return DG_ERR_ARG;
+    dg::g_tile_var[p + 1] = variant;
+    return DG_OK;
+}
+
+int dg_get_tile_variant(int p) { return (p < 0 || p > DG_MAX_P) ? -1 : dg::g_tile_var[p + 1]; }
+
+dg_status dg_tile_shape(int p, int variant, int *tx, int *ty)
+{
+    if (!tx || !ty) return DG_ERR_ARG;
+    int th;
+    size_t sm;
+    if (p < 0 || p > DG_MAX_P || !dg::tile_code_info((p + 1) * 8 + variant, tx, ty, &th, &sm))
+        return DG_ERR_ARG;
+    return DG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batches: many independent float meshes advanced by one launch per stage
+// ---------------------------------------------------------------------------
+struct dg_batch {
+    int n = 0;
+    std::vector<dg::InstDev> inst;      // host copy of the descriptors
+    std::vector<dg::BatchItem> items;   // host copy of the work list
+    std::vector<long long> dofs;
+    dg::InstDev *d_inst = nullptr;
+    dg::BatchItem *d_items = nullptr;
+    double *d_dt = nullptr;
+    unsigned long long *d_lam = nullptr;
+    int *d_err = nullptr;
+    double *d_partials = nullptr;
+    std::vector<void *> qt;             // second states owned by the batch
+    int threads = 256, grid = 1;    // CFL launches
+    // per size class of the stage kernel: item range, shared memory, grid
+    int cbeg[2] = {0, 0}, cend[2] = {0, 0}, cgrid[2] = {1, 1};
+    size_t csmem[2] = {0, 0};
+    // recorded graphs of one step (ends with the copy back) and of two steps
+    // (ends in Q by itself), and the cfl they were recorded with
+    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+    double graph_cfl[3] = {-1.0, -1.0, -1.0};
+};
+
+namespace {
+
+void batch_free(dg_batch *b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    for (int k = 1; k <= 2; ++k)
+        if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+    for (void *p : b->qt) cudaFree(p);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_items);
+    cudaFree(b->d_dt);
+    cudaFree(b->d_lam);
+    cudaFree(b->d_err);
+    cudaFree(b->d_partials);
+    delete b;
+}
+
+// Tile variant of order N inside a batch.  The batch runs every tile with one
+// block size (256 threads, 352 when a p = 6 instance is present), so the tile
+// that fills a block best is taken: the variants with the most nodes not
+// above 256 (all of them above 256 only for N = 7); among those, the tuning
+// table's choice if it is one of them, else the first.
+int batch_tile_variant(int N)
+{
+    int best_nodes = -1, pick = 0;
+    const int tuned = dg::tile_variant(N);
+    for (int v = 0; v < 8; ++v) {
+        int tx, ty, th;
+        size_t sm;
+        if (!dg::tile_code_info(N * 8 + v, &tx, &ty, &th, &sm)) break;
+        const int nodes = tx * ty * N * N * N;
+        const int score = nodes <= 256 ? nodes : 0;
+        if (score > best_nodes || (score == best_nodes && v == tuned)) {
+            best_nodes = score;
+            pick = v;
+        }
+    }
+    return pick;
+}
+
+// The kernels of `nsteps` (1 or 2) steps on stream s.  Per step: the CFL
+// time step of every instance (read from the buffer holding the state), then
+// five fused stages alternating between Q and the second state Qt.  One step
+// ends in Qt and is followed by a copy back into Q (one memcpy per
+// instance); two steps end in Q by themselves.
+cudaError_t batch_enqueue(const dg_batch *b, double cfl, int nsteps, cudaStream_t s)
+{
+    static const double kA[5] = {0.0,
+                                 -567301805773.0 / 1357537059087.0,
+                                 -2404267990393.0 / 2016746695238.0,
+                                 -3550918686646.0 / 2091501179385.0,
+                                 -1275806237668.0 / 842570457699.0};
+    static const double kB[5] = {1432997174477.0 / 9575080441755.0,
+                                 5161836677717.0 / 13612068292357.0,
+                                 1720146321549.0 / 2090206949498.0,
+                                 3134564353537.0 / 4481467310338.0,
+                                 2277821191437.0 / 14882151754819.0};
+    const int ni = (int)b->items.size();
+    cudaError_t e = cudaSuccess;
+    int parity = 0;  // 0: the state is in Q
+    for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
+        e = dg::batch_cfl(b->d_items, ni, b->d_inst, b->n, parity, cfl, b->d_err, b->grid,
+                          b->threads, s);
+        for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
+            for (int c = 0; c < 2 && e == cudaSuccess; ++c)
+                if (b->cend[c] > b->cbeg[c])
+                    e = dg::batch_stage(b->d_items + b->cbeg[c], b->cend[c] - b->cbeg[c],
+                                        b->d_inst, parity, (float)kA[st], (float)kB[st], c,
+                                        b->cgrid[c], b->csmem[c], s);
+            parity ^= 1;
+        }
+    }
+    if (parity == 1)
+        for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+            const dg::InstDev &I = b->inst[i];
+            const int N = I.g.p + 1;
+            const size_t bytes = (size_t)dg::NF * (size_t)I.g.E * N * N * N * sizeof(float);
+            e = cudaMemcpyAsync(I.Q, I.Qt, bytes, cudaMemcpyDeviceToDevice, s);
+        }
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
+{
+    if (!out) return DG_ERR_ARG;
+    *out = nullptr;
+    if (n < 1 || !desc) return DG_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        const dg_instance &d = desc[i];
+        if (d.nx < 1 || d.ny < 1 || d.nz < 1 || !d.Q || !d.dQ || d.Q == d.dQ) return DG_ERR_ARG;
+        if (d.Qt && (d.Qt == d.Q || d.Qt == d.dQ || !aligned16(d.Qt))) return DG_ERR_ARG;
+        if (!aligned16(d.Q) || !aligned16(d.dQ)) return DG_ERR_ARG;
+        if (!finite_pos(d.Lx) || !finite_pos(d.Ly) || !finite_pos(d.Lz)) return DG_ERR_ARG;
+        if (!std::isfinite(d.x0) || !std::isfinite(d.y0) || !std::isfinite(d.z0)) return DG_ERR_ARG;
+        if (!(std::isfinite(d.gamma) && d.gamma > 1.0)) return DG_ERR_ARG;
+        if (d.p < 0 || d.p > DG_MAX_P) return DG_ERR_UNSUPPORTED;
+        const long long E = (long long)d.nx * d.ny * d.nz;
+        if (E * (d.p + 1) * (d.p + 1) * (d.p + 1) >= (1LL << 40)) return DG_ERR_ARG;
+    }
+    dg_batch *b = new (std::nothrow) dg_batch();
+    if (!b) return DG_ERR_OOM;
+    b->n = n;
+    b->inst.resize(n);
+    cudaError_t err = cudaSuccess;
+    for (int i = 0; i < n && err == cudaSuccess; ++i) {
+        const dg_instance &d = desc[i];
+        const int N = d.p + 1;
+        dg::InstDev &I = b->inst[i];
+        std::memset(&I, 0, sizeof(I));
+        dg::Geo &g = I.g;
+        g.nx = d.nx; g.ny = d.ny; g.nz = d.nz; g.p = d.p;
+        g.E = (long long)d.nx * d.ny * d.nz;
+        g.x0 = d.x0; g.y0 = d.y0; g.z0 = d.z0;
+        g.hx = d.Lx / d.nx; g.hy = d.Ly / d.ny; g.hz = d.Lz / d.nz;
+        g.gamma = d.gamma;
+        g.J = g.hx * g.hy * g.hz / 8.0;
+        g.hmin = std::fmin(g.hx, std::fmin(g.hy, g.hz));
+        Basis B;
+        make_basis(N, B);
+        for (int a = 0; a < N; ++a) {
+            g.xi[a] = (double)B.x[a];
+            g.w[a] = (double)B.w[a];
+        }
+        const double gf[3] = {2.0 / g.hx, 2.0 / g.hy, 2.0 / g.hz};
+        fill_ops(B, gf, I.T);
+        fill_gas(d.gamma, I.T);
+        I.Q = (float *)d.Q;
+        I.dQ = (float *)d.dQ;
+        I.code = N * 8 + batch_tile_variant(N);
+        const size_t bytes = (size_t)dg::NF * (size_t)g.E * N * N * N * sizeof(float);
+        void *qt = d.Qt;
+        if (!qt) {
+            err = cudaMalloc(&qt, bytes);
+            if (err == cudaSuccess) b->qt.push_back(qt);  // the batch's own
+        }
+        I.Qt = (float *)qt;
+        b->dofs.push_back(g.E * N * N * N);
+    }
+    if (err == cudaSuccess) err = cudaMalloc((void **)&b->d_dt, sizeof(double) * n);
+    if (err == cudaSuccess) err = cudaMalloc((void **)&b->d_lam, sizeof(unsigned long long) * n);
+    if (err == cudaSuccess) err = cudaMalloc((void **)&b->d_err, sizeof(int));
+    if (err == cudaSuccess)
+        err = cudaMalloc((void **)&b->d_partials, (size_t)dg::kNormBlocks * 8 * sizeof(double));
+    if (err == cudaSuccess) err = cudaMemset(b->d_lam, 0, sizeof(unsigned long long) * n);
+    if (err == cudaSuccess) err = cudaMemset(b->d_err, 0, sizeof(int));
+    if (err != cudaSuccess) {
+        dg_status st = cuda_status(err);
+        cudaGetLastError();
+        batch_free(b);
+        return st;
+    }
+    // work list: every tile of every instance, grouped by tile code
+    for (int i = 0; i < n; ++i) {
+        dg::InstDev &I = b->inst[i];
+        I.dt = b->d_dt + i;
+        I.lam_bits = b->d_lam + i;
+        int tx, ty, th;
+        size_t sm;
+        if (!dg::tile_code_info(I.code, &tx, &ty, &th, &sm)) {
+            batch_free(b);
+            return DG_ERR_UNSUPPORTED;
+        }
+        const int c = dg::batch_code_class(I.code);
+        b->csmem[c] = std::max(b->csmem[c], sm);
+        const long long nt = dg::tile_count(I.g, tx, ty);
+        for (long long t = 0; t < nt; ++t) b->items.push_back({i, I.code, t});
+    }
+    std::stable_sort(b->items.begin(), b->items.end(),
+                     [](const dg::BatchItem &x, const dg::BatchItem &y) { return x.code < y.code; });
+    err = cudaMalloc((void **)&b->d_inst, sizeof(dg::InstDev) * n);
+    if (err == cudaSuccess) err = cudaMalloc((void **)&b->d_items, sizeof(dg::BatchItem) * b->items.size());
+    if (err == cudaSuccess)
+        err = cudaMemcpy(b->d_inst, b->inst.data(), sizeof(dg::InstDev) * n, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(b->d_items, b->items.data(), sizeof(dg::BatchItem) * b->items.size(),
+                         cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) {
+        dg_status st = cuda_status(err);
+        cudaGetLastError();
+        batch_free(b);
+        return st;
+    }
+    // persistent grids: as many CTAs as fit on the GPU at once, per size
+    // class (the items are sorted by code, so each class is one range)
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ni = (int)b->items.size();
+    int split = 0;
+    while (split < ni && dg::batch_code_class(b->items[split].code) == 0) ++split;
+    b->cbeg[0] = 0; b->cend[0] = split;
+    b->cbeg[1] = split; b->cend[1] = ni;
+    for (int c = 0; c < 2; ++c) {
+        const long long cnt = b->cend[c] - b->cbeg[c];
+        if (cnt == 0) continue;
+        const long long per_sm = dg::batch_stage_blocks_per_sm(c, b->csmem[c]);
+        b->cgrid[c] = (int)std::min<long long>((long long)sms * per_sm, cnt);
+    }
+    b->grid = (int)std::min<long long>((long long)sms * 8, (long long)ni);
+    *out = b;
+    return DG_OK;
+}
+
+void dg_batch_destroy(dg_batch *b) { batch_free(b); }
+
+dg_status dg_batch_sizes(const dg_batch *b, int64_t *n_dof, int64_t *n_items)
+{
+    if (!b) return DG_ERR_ARG;
+    long long s = 0;
+    for (long long d : b->dofs) s += d;
+    if (n_dof) *n_dof = s;
+    if (n_items) *n_items = (int64_t)b->items.size();
+    return DG_OK;
+}
+
+dg_status dg_batch_state_init(const dg_batch *b, int idx, dg_init_kind kind, const double *params,
+                              int nparams, void *stream)
+{
+    if (!b || idx < 0 || idx >= b->n) return DG_ERR_ARG;
+    int need = kind == DG_INIT_UNIFORM ? 5 : kind == DG_INIT_VORTEX ? 7 : kind == DG_INIT_TGV ? 3 : -1;
+    if (need < 0 || nparams < need || nparams > 8 || !params) return DG_ERR_ARG;
+    double pr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < nparams; ++i) {
+        if (!std::isfinite(params[i])) return DG_ERR_ARG;
+        pr[i] = params[i];
+    }
+    dg::Work w;
+    return cuda_status(dg::Launch<float>::init(b->inst[idx].g, kind, pr, b->inst[idx].Q, w,
+                                               as_stream(stream)));
+}
+
+dg_status dg_batch_step(dg_batch *b, double cfl, int nsteps, int use_graph, void *stream)
+{
+    if (!b || !finite_pos(cfl) || nsteps < 0) return DG_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    if (!use_graph) {
+        cudaError_t e = cudaSuccess;
+        for (int k = nsteps; k > 0 && e == cudaSuccess; k -= 2)
+            e = batch_enqueue(b, cfl, k >= 2 ? 2 : 1, s);
+        return cuda_status(e);
+    }
+    if (!s) return DG_ERR_ARG;  // capture needs a created stream, not the legacy default
+    for (int k = nsteps; k > 0; k -= 2) {
+        const int n = k >= 2 ? 2 : 1;
+        if (!b->exec[n] || b->graph_cfl[n] != cfl) {
+            if (b->exec[n]) {
+                cudaGraphExecDestroy(b->exec[n]);
+                b->exec[n] = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return DG_ERR_CUDA;
+            cudaError_t ek = batch_enqueue(b, cfl, n, s);
+            e = cudaStreamEndCapture(s, &graph);
+            if (ek != cudaSuccess || e != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return DG_ERR_CUDA;
+            }
+            e = cudaGraphInstantiate(&b->exec[n], graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                b->exec[n] = nullptr;
+                return DG_ERR_CUDA;
+            }
+            b->graph_cfl[n] = cfl;
+        }
+        cudaError_t e = cudaGraphLaunch(b->exec[n], s);
+        if (e != cudaSuccess) return DG_ERR_CUDA;
+    }
+    return DG_OK;
+}
+
+dg_status dg_batch_dt(const dg_batch *b, double *dt_host)
+{
+    if (!b || !dt_host) return DG_ERR_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(dt_host, b->d_dt, sizeof(double) * b->n, cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+}
+
+dg_status dg_batch_norms(const dg_batch *b, int idx, const void *Qref, double *out, void *stream)
+{
+    if (!b || idx < 0 || idx >= b->n || !out) return DG_ERR_ARG;
+    dg::Work w;
+    w.partials = b->d_partials;
+    return cuda_status(dg::Launch<float>::norms(b->inst[idx].g, b->inst[idx].Q,
+                                                (const float *)Qref, out, w, as_stream(stream)));
+}
+
+dg_status dg_batch_last_error(const dg_batch *b)
+{
+    if (!b) return DG_ERR_ARG;
+    int flag = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return DG_ERR_CUDA;
+    return flag ? DG_ERR_NONFINITE : DG_OK;
 }
 
 const char *dg_status_string(dg_status s)

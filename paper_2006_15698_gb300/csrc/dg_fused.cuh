@@ -1,0 +1,482 @@
+// dg_fused.cuh -- the float form's fused single-pass RK stage (faces + volume
+// + lift + update in one kernel), for one mesh and for a batch of independent
+// meshes in one persistent launch.  Included by dg_kernels.cuh.
+//
+// For the float form the stage is bound by DRAM traffic and instruction
+// issue, not by a narrow pipe, so one kernel does all of it: a CTA stages a
+// tile of elements' states and fluxes in shared memory, computes the
+// Lax-Friedrichs flux on all six faces of each of its elements (the
+// neighbour's trace is interpolated from the neighbour's face-normal node
+// lines, read through L2, or from shared memory when the neighbour is in the
+// same tile), then the derivative, lift and update.  Each interface flux is
+// evaluated by both adjacent tiles from bitwise-identical inputs in the same
+// operation order, so both see the same value and discrete conservation holds
+// as in the two-kernel form.  DRAM traffic per stage is Q read, dQ
+// read/written and Q' written: the output goes to a second state buffer,
+// because neighbouring tiles still read the input state.
+//
+// A tile is TX x TY elements of one z layer (x fastest); the shape per
+// polynomial order is chosen by the autotuner among the variants below.
+#pragma once
+
+// (included inside namespace dg)
+
+// single-instruction float approximations (PTX rcp.approx / sqrt.approx,
+// relative error of order 2^-23, the float form's own rounding level)
+__device__ __forceinline__ float fast_rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float fast_sqrt(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <int DIR>
+__device__ __forceinline__ void normal_flux_f(const float q[NF], float gamma, float gm1,
+                                              float f[NF], float &speed)
+{
+    const float rinv = fast_rcp(q[0]);
+    const float mm = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    const float p = gm1 * (q[4] - 0.5f * mm * rinv);
+    const float mn = q[1 + DIR];
+    const float un = mn * rinv;
+    f[0] = mn;
+    f[1] = q[1] * un + (DIR == 0 ? p : 0.0f);
+    f[2] = q[2] * un + (DIR == 1 ? p : 0.0f);
+    f[3] = q[3] * un + (DIR == 2 ? p : 0.0f);
+    f[4] = (q[4] + p) * un;
+    speed = fabsf(un) + fast_sqrt(gamma * p * rinv);
+}
+
+// N consecutive floats; vector loads when the line is 8- or 16-byte aligned
+// (N even: every line starts at a multiple of N floats from an aligned base)
+template <int N>
+__device__ __forceinline__ void load_line(const float *p, float v[N])
+{
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int a = 0; a < N; a += 4) {
+            const float4 t = *reinterpret_cast<const float4 *>(p + a);
+            v[a] = t.x; v[a + 1] = t.y; v[a + 2] = t.z; v[a + 3] = t.w;
+        }
+    } else if constexpr (N % 2 == 0) {
+#pragma unroll
+        for (int a = 0; a < N; a += 2) {
+            const float2 t = *reinterpret_cast<const float2 *>(p + a);
+            v[a] = t.x; v[a + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < N; ++a) v[a] = p[a];
+    }
+}
+
+// Trace of an element on a face in direction DIR at node line (t1, t2):
+// sum_c l[c] Q(node c along DIR), from `src` (the element's field planes at
+// plane stride `pstride`); the same arithmetic for shared and global sources.
+template <int N, int DIR>
+__device__ __forceinline__ void line_trace(const float *src, long long pstride, int base,
+                                           const float *l, float q[NF])
+{
+    constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? N : N * N);
+#pragma unroll
+    for (int n = 0; n < NF; ++n) {
+        float v[N];
+        if constexpr (DIR == 0) {
+            load_line<N>(src + n * pstride + base, v);
+        } else {
+#pragma unroll
+            for (int c = 0; c < N; ++c) v[c] = src[n * pstride + base + c * stride];
+        }
+        float s = 0.0f;
+#pragma unroll
+        for (int c = 0; c < N; ++c) s += l[c] * v[c];
+        q[n] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tile shapes
+// ---------------------------------------------------------------------------
+
+// Variants per N (= p + 1): (TX, TY) elements per tile.
+template <int N, int V>
+struct TileShape;
+template <> struct TileShape<1, 0> { static constexpr int TX = 128, TY = 1; };
+template <> struct TileShape<1, 1> { static constexpr int TX = 256, TY = 1; };
+template <> struct TileShape<2, 0> { static constexpr int TX = 32, TY = 1; };
+template <> struct TileShape<2, 1> { static constexpr int TX = 16, TY = 2; };
+template <> struct TileShape<2, 2> { static constexpr int TX = 8, TY = 4; };
+template <> struct TileShape<3, 0> { static constexpr int TX = 9, TY = 1; };
+template <> struct TileShape<3, 1> { static constexpr int TX = 3, TY = 3; };
+template <> struct TileShape<4, 0> { static constexpr int TX = 4, TY = 1; };
+template <> struct TileShape<4, 1> { static constexpr int TX = 2, TY = 2; };
+template <> struct TileShape<5, 0> { static constexpr int TX = 2, TY = 1; };
+template <> struct TileShape<5, 1> { static constexpr int TX = 1, TY = 1; };
+template <> struct TileShape<6, 0> { static constexpr int TX = 1, TY = 1; };
+template <> struct TileShape<7, 0> { static constexpr int TX = 1, TY = 1; };
+constexpr int kTileVariants[8] = {0, 2, 3, 2, 2, 2, 1, 1};  // per N
+
+template <int N, int TX, int TY>
+struct FusedTile {
+    static constexpr int N2 = N * N, N3 = N * N * N;
+    static constexpr int EPB = TX * TY;
+    static constexpr int THREADS = ((EPB * N3 + 31) / 32) * 32;
+    // face tasks: six faces, each a warp-aligned segment of EPB N^2 points
+    static constexpr int SEGF = ((EPB * N2 + 31) / 32) * 32;
+    // per-element strides in shared memory, padded to 16 (mod 32) floats so
+    // that two elements touched by one warp fall into different bank halves
+    static constexpr int pad16(int x) { return x + ((16 - x % 32) + 32) % 32; }
+    static constexpr int FSTR = pad16(3 * NF * N3);      // fluxes [3][NF][N3], direction-major
+    static constexpr int QSTR = pad16(NF * N3);          // state [NF][N3]
+    static constexpr int HSTR = pad16(3 * NF * N2 * 2);  // face fluxes [3][NF][N2][(-,+)]
+    // fluxes, state, face fluxes (floats), then the neighbour table [EPB][6]
+    static constexpr size_t FLOATS = (size_t)EPB * (FSTR + QSTR + HSTR);
+    static constexpr size_t BYTES = ((FLOATS * sizeof(float) + 15) / 16) * 16 + EPB * 6 * 8;
+};
+
+
+// ---------------------------------------------------------------------------
+// one tile of the fused stage
+// ---------------------------------------------------------------------------
+
+// Neighbour table entry: >= 0 a global element index, < 0 the in-tile index
+// -(local + 1) of a neighbour that sits in the same tile.
+template <int N, int DIR, int TX, int TY>
+__device__ __forceinline__ void fused_face(const float *__restrict__ Qin, const float *sQ,
+                                           float *sH, const long long *sNb, const Ops<float> &T,
+                                           long long E, int el, int side, int pt)
+{
+    using FT = FusedTile<N, TX, TY>;
+    constexpr int N2 = N * N, N3 = N * N * N;
+    const int t1 = pt % N, t2 = pt / N;
+    const int base = DIR == 0 ? (t2 * N + t1) * N : (DIR == 1 ? t2 * N2 + t1 : t2 * N + t1);
+    const long long nb = sNb[el * 6 + 2 * DIR + side];
+    // own trace at the face's end of the element, the neighbour's at the other end
+    float qo[NF], qn[NF];
+    line_trace<N, DIR>(sQ + (size_t)el * FT::QSTR, N3, base, side ? T.lp : T.lm, qo);
+    if (nb < 0)
+        line_trace<N, DIR>(sQ + (size_t)(-nb - 1) * FT::QSTR, N3, base, side ? T.lm : T.lp, qn);
+    else
+        line_trace<N, DIR>(Qin + nb * N3, E * N3, base, side ? T.lm : T.lp, qn);
+    // left and right states by value selects (a pointer select between two
+    // local arrays would force them out of registers)
+    float qL[NF], qR[NF];
+#pragma unroll
+    for (int n = 0; n < NF; ++n) {
+        qL[n] = side ? qo[n] : qn[n];
+        qR[n] = side ? qn[n] : qo[n];
+    }
+    float fL[NF], fR[NF], sL, sR;
+    normal_flux_f<DIR>(qL, T.gamma, T.gm1, fL, sL);
+    normal_flux_f<DIR>(qR, T.gamma, T.gm1, fR, sR);
+    const float lam = fmaxf(sL, sR);
+    // (-, +) pair of the direction's two faces at this face point
+    float *h = sH + (size_t)el * FT::HSTR + (DIR * NF * N2 + pt) * 2 + side;
+#pragma unroll
+    for (int n = 0; n < NF; ++n) h[n * N2 * 2] = (fL[n] + fR[n]) - lam * (qR[n] - qL[n]);
+}
+
+// One tile of the stage with blockDim.x >= TX*TY*N^3 threads (one per node;
+// extra threads only help with the face tasks).  MODE 0 writes the rhs to
+// Out, MODE 1 the LSERK stage update (dQ <- A dQ + dt R, Out <- Qin + B dQ).
+// Ends with a barrier, so a persistent caller may reuse `smem` at once.
+template <int N, int TX, int TY, int MODE>
+__device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float *__restrict__ Out,
+                                           float *__restrict__ dQ, const Ops<float> &T,
+                                           const Geo &g, long long tile, float A, float B,
+                                           float dtr, unsigned char *smem)
+{
+    using FT = FusedTile<N, TX, TY>;
+    constexpr int N2 = FT::N2, N3 = FT::N3, EPB = FT::EPB, SEGF = FT::SEGF;
+    constexpr int FSTR = FT::FSTR, QSTR = FT::QSTR, HSTR = FT::HSTR;
+    float *sF = reinterpret_cast<float *>(smem);  // [EPB][FSTR]
+    float *sQ = sF + EPB * FSTR;                  // [EPB][QSTR]
+    float *sH = sQ + EPB * QSTR;                  // [EPB][HSTR]
+    long long *sNb = reinterpret_cast<long long *>(smem + (FT::BYTES - EPB * 6 * 8));
+
+    // tile -> element coordinates of its corner
+    const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY;
+    const int bx = (int)(tile % ntx);
+    const int by = (int)((tile / ntx) % nty);
+    const int bz = (int)(tile / ((long long)ntx * nty));
+    const int ex0 = bx * TX, ey0 = by * TY;
+
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int el = tid / N3;
+    const int node = tid - el * N3;
+    const int a = el % TX, b = el / TX;
+    const bool in_tile = el < EPB;
+    const bool active = in_tile && ex0 + a < g.nx && ey0 + b < g.ny;
+    const long long e = (long long)(ex0 + a) + (long long)g.nx * ((ey0 + b) + (long long)g.ny * bz);
+    const int i = node % N, j = (node / N) % N, k = node / N2;
+
+    for (int t = tid; t < EPB * 6; t += nthr) {  // the six neighbours of every element of the tile
+        const int te = t / 6, f = t - te * 6;
+        const int ta = te % TX, tb = te / TX;
+        const int d = f >> 1, s = (f & 1) ? 1 : -1;
+        int cx = ex0 + ta, cy = ey0 + tb, cz = bz;
+        long long nb = 0;
+        if (cx < g.nx && cy < g.ny) {
+            if (d == 0) cx = (cx + s + g.nx) % g.nx;
+            else if (d == 1) cy = (cy + s + g.ny) % g.ny;
+            else cz = (cz + s + g.nz) % g.nz;
+            const int la = cx - ex0, lb = cy - ey0;
+            if (cz == bz && la >= 0 && la < TX && lb >= 0 && lb < TY)
+                nb = -(long long)(lb * TX + la) - 1;
+            else
+                nb = (long long)cx + (long long)g.nx * (cy + (long long)g.ny * cz);
+        }
+        sNb[t] = nb;
+    }
+
+    float q[NF];
+    if (active) {
+#pragma unroll
+        for (int n = 0; n < NF; ++n) {
+            q[n] = Qin[sidx(n, e, node, g.E, N3)];
+            sQ[el * QSTR + n * N3 + node] = q[n];
+        }
+        const float rinv = fast_rcp(q[0]);
+        const float u = q[1] * rinv, v = q[2] * rinv, w = q[3] * rinv;
+        const float p = T.gm1 * (q[4] - 0.5f * (q[1] * u + q[2] * v + q[3] * w));
+        const float ep = q[4] + p;
+        // direction-major node order: the line a contraction reads is contiguous
+        float *sx = sF + (size_t)el * FSTR + 0 * NF * N3 + (k * N + j) * N + i;
+        float *sy = sF + (size_t)el * FSTR + 1 * NF * N3 + (k * N + i) * N + j;
+        float *sz = sF + (size_t)el * FSTR + 2 * NF * N3 + (j * N + i) * N + k;
+        sx[0 * N3] = q[1];
+        sx[1 * N3] = q[1] * u + p;
+        sx[2 * N3] = q[2] * u;
+        sx[3 * N3] = q[3] * u;
+        sx[4 * N3] = ep * u;
+        sy[0 * N3] = q[2];
+        sy[1 * N3] = q[1] * v;
+        sy[2 * N3] = q[2] * v + p;
+        sy[3 * N3] = q[3] * v;
+        sy[4 * N3] = ep * v;
+        sz[0 * N3] = q[3];
+        sz[1 * N3] = q[1] * w;
+        sz[2 * N3] = q[2] * w;
+        sz[3 * N3] = q[3] * w + p;
+        sz[4 * N3] = ep * w;
+    }
+    __syncthreads();
+
+    // the six faces of every element of the tile, face-major so that a warp
+    // works on one (direction, side)
+    for (int t = tid; t < 6 * SEGF; t += nthr) {
+        const int face = t / SEGF;
+        const int r = t - face * SEGF;
+        if (r >= EPB * N2) continue;
+        const int el2 = r / N2;
+        const int pt = r - el2 * N2;
+        if (ex0 + el2 % TX >= g.nx || ey0 + el2 / TX >= g.ny) continue;
+        const int side = face & 1;
+        if (face < 2) fused_face<N, 0, TX, TY>(Qin, sQ, sH, sNb, T, g.E, el2, side, pt);
+        else if (face < 4) fused_face<N, 1, TX, TY>(Qin, sQ, sH, sNb, T, g.E, el2, side, pt);
+        else fused_face<N, 2, TX, TY>(Qin, sQ, sH, sNb, T, g.E, el2, side, pt);
+    }
+    __syncthreads();
+
+    if (active) {
+        const int px = k * N + j, py = k * N + i, pz = j * N + i;
+        const float *h = sH + (size_t)el * HSTR;
+        const float *f = sF + (size_t)el * FSTR;
+#pragma unroll
+        for (int n = 0; n < NF; ++n) {
+            float vx[N], vy[N], vz[N];
+            load_line<N>(f + 0 * NF * N3 + n * N3 + (k * N + j) * N, vx);
+            load_line<N>(f + 1 * NF * N3 + n * N3 + (k * N + i) * N, vy);
+            load_line<N>(f + 2 * NF * N3 + n * N3 + (j * N + i) * N, vz);
+            float acc = 0.0f;
+#pragma unroll
+            for (int c = 0; c < N; ++c) acc += T.D[0][i][c] * vx[c];
+#pragma unroll
+            for (int c = 0; c < N; ++c) acc += T.D[1][j][c] * vy[c];
+#pragma unroll
+            for (int c = 0; c < N; ++c) acc += T.D[2][k][c] * vz[c];
+            // lift: one (-, +) pair of face fluxes per direction
+            const float2 hx = *reinterpret_cast<const float2 *>(h + ((0 * NF + n) * N2 + px) * 2);
+            const float2 hy = *reinterpret_cast<const float2 *>(h + ((1 * NF + n) * N2 + py) * 2);
+            const float2 hz = *reinterpret_cast<const float2 *>(h + ((2 * NF + n) * N2 + pz) * 2);
+            acc += T.Lm[0][i] * hx.x - T.Lp[0][i] * hx.y;
+            acc += T.Lm[1][j] * hy.x - T.Lp[1][j] * hy.y;
+            acc += T.Lm[2][k] * hz.x - T.Lp[2][k] * hz.y;
+
+            const long long o = sidx(n, e, node, g.E, N3);
+            if (MODE == 0) {
+                Out[o] = acc;
+            } else {
+                const float d = (A == 0.0f ? 0.0f : A * dQ[o]) + dtr * acc;
+                dQ[o] = d;
+                Out[o] = q[n] + B * d;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// one mesh: one tile per CTA
+template <int N, int V, int MODE>
+__global__ void __launch_bounds__(FusedTile<N, TileShape<N, V>::TX, TileShape<N, V>::TY>::THREADS)
+    fused_stage_kernel(const float *__restrict__ Qin, float *__restrict__ Out,
+                       float *__restrict__ dQ, const Ops<float> T, const Geo g, float A, float B,
+                       const double *__restrict__ dt)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const float dtr = MODE == 1 ? (float)(*dt) : 0.0f;
+    fused_tile<N, TileShape<N, V>::TX, TileShape<N, V>::TY, MODE>(Qin, Out, dQ, T, g, blockIdx.x,
+                                                                   A, B, dtr, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// batches: many independent meshes, one persistent launch per stage
+// ---------------------------------------------------------------------------
+
+#define DG_FOR_EACH_CODE(X) \
+    X(1, 0) X(1, 1) X(2, 0) X(2, 1) X(2, 2) X(3, 0) X(3, 1) X(4, 0) X(4, 1) X(5, 0) X(5, 1) \
+    X(6, 0) X(7, 0)
+
+// Two size classes, so that the registers of the large p = 6 tiles do not
+// cap the occupancy of all the others: class 0 holds the tile codes with
+// N <= 6 (every tile fits 256 threads; four resident CTAs bound registers to
+// 64), class 1 the N = 7 tiles (343 nodes, 352 threads).
+// One tile of a batch, compiled as a separate function: each tile code keeps
+// its own register allocation instead of sharing the switch's worst case.
+template <int N, int V, int MODE>
+__device__ __noinline__ void batched_tile(const float *__restrict__ Qin, float *__restrict__ Out,
+                                          float *__restrict__ dQ, const Ops<float> &T,
+                                          const Geo &g, long long tile, float A, float B,
+                                          float dtr, unsigned char *smem)
+{
+    fused_tile<N, TileShape<N, V>::TX, TileShape<N, V>::TY, MODE>(Qin, Out, dQ, T, g, tile, A, B,
+                                                                   dtr, smem);
+}
+
+#define DG_FOR_EACH_CODE_C0(X) \
+    X(1, 0) X(1, 1) X(2, 0) X(2, 1) X(2, 2) X(3, 0) X(3, 1) X(4, 0) X(4, 1) X(5, 0) X(5, 1) \
+    X(6, 0)
+#define DG_FOR_EACH_CODE_C1(X) X(7, 0)
+constexpr int kBatchClassThreads[2] = {256, 352};
+__host__ __device__ constexpr int batch_class(int code) { return (code >> 3) == 7 ? 1 : 0; }
+
+template <int MODE, int CLASS>
+__global__ void __launch_bounds__(CLASS == 0 ? 256 : 352, CLASS == 0 ? 4 : 2)
+    batched_stage_kernel(const BatchItem *__restrict__ items, int nitems,
+                         const InstDev *__restrict__ inst, int parity, float A, float B)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem item = items[it];
+        const InstDev &d = inst[item.inst];
+        const float *src = parity == 0 ? d.Q : d.Qt;
+        float *dst = parity == 0 ? d.Qt : d.Q;
+        const float dtr = MODE == 1 ? (float)(*d.dt) : 0.0f;
+#define DG_CASE(NN, VV)                                                                       \
+    case NN * 8 + VV:                                                                         \
+        batched_tile<NN, VV, MODE>(src, dst, d.dQ, d.T, d.g, item.tile, A, B, dtr, smem_raw); \
+        break;
+        if constexpr (CLASS == 0) {
+            switch (item.code) {
+                DG_FOR_EACH_CODE_C0(DG_CASE)
+            default: break;
+            }
+        } else {
+            switch (item.code) {
+                DG_FOR_EACH_CODE_C1(DG_CASE)
+            default: break;
+            }
+        }
+#undef DG_CASE
+    }
+}
+
+// Lambda of every instance: node speeds of each tile in float, maximum in
+// double (bit patterns of non-negative doubles; NaN above every finite value).
+template <int N, int TX, int TY>
+__device__ __forceinline__ double tile_speed_max(const float *__restrict__ Q, const Geo &g,
+                                                 long long tile, float gamma, bool &bad)
+{
+    const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY;
+    const int bx = (int)(tile % ntx), by = (int)((tile / ntx) % nty);
+    const int bz = (int)(tile / ((long long)ntx * nty));
+    constexpr int N3 = N * N * N;
+    double m = 0.0;
+    for (int t = threadIdx.x; t < TX * TY * N3; t += blockDim.x) {
+        const int el = t / N3, node = t - el * N3;
+        const int ex = bx * TX + el % TX, ey = by * TY + el / TX;
+        if (ex >= g.nx || ey >= g.ny) continue;
+        const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * bz);
+        const long long o = e * N3 + node, pl = g.E * N3;
+        const float r = Q[o], mx = Q[pl + o], my = Q[2 * pl + o], mz = Q[3 * pl + o],
+                    E = Q[4 * pl + o];
+        const float rinv = 1.0f / r;
+        const float u = mx * rinv, v = my * rinv, w = mz * rinv;
+        const float p = (gamma - 1.0f) * (E - 0.5f * r * (u * u + v * v + w * w));
+        if (!(r > 0.0f) || !(p > 0.0f)) {
+            bad = true;
+            continue;
+        }
+        const float c = sqrtf(gamma * p * rinv);
+        m = fmax(m, (double)((fabsf(u) + c) + (fabsf(v) + c) + (fabsf(w) + c)));
+    }
+    return m;
+}
+
+static __global__ void __launch_bounds__(512)
+    batched_cfl_kernel(const BatchItem *__restrict__ items, int nitems,
+                       const InstDev *__restrict__ inst, int parity, int *err)
+{
+    __shared__ unsigned long long red[16];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem item = items[it];
+        const InstDev &d = inst[item.inst];
+        bool bad = false;
+        double m = 0.0;
+        switch (item.code) {
+#define DG_CASE(NN, VV)                                                                          \
+    case NN * 8 + VV:                                                                            \
+        m = tile_speed_max<NN, TileShape<NN, VV>::TX, TileShape<NN, VV>::TY>(                    \
+            parity == 0 ? d.Q : d.Qt, d.g, item.tile, \
+                                                                              d.T.gamma, bad);    \
+        break;
+            DG_FOR_EACH_CODE(DG_CASE)
+#undef DG_CASE
+        default: break;
+        }
+        if (bad) {
+            atomicOr(err, 1);
+            m = __longlong_as_double(0x7ff8000000000000LL);
+        }
+        unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long x = __shfl_xor_sync(0xffffffffu, bits, o);
+            bits = x > bits ? x : bits;
+        }
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bits;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long mb = red[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mb = red[w] > mb ? red[w] : mb;
+            atomicMax(d.lam_bits, mb);
+        }
+        __syncthreads();
+    }
+}
+
+static __global__ void batched_cfl_finalize_kernel(const InstDev *__restrict__ inst, int n, double cfl)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const InstDev &d = inst[i];
+        const double lam = __longlong_as_double((long long)*d.lam_bits);
+        *d.dt = __ddiv_rn(__dmul_rn(cfl, d.g.hmin), __dmul_rn(2.0 * d.g.p + 1.0, lam));
+        *d.lam_bits = 0ull;
+    }
+}

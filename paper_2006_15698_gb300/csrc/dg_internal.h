@@ -96,6 +96,51 @@ struct Work {
 
 constexpr int kNormBlocks = 1024;  // fixed partition of the norms reduction
 
+// Tile variant of the float form's fused stage per N = p + 1 (process-wide
+// tuning table, set through dg_set_tile_variant; read at each launch).
+int tile_variant(int N);
+
+// tiles of TX x TY elements covering a mesh: ceil(nx/TX) x ceil(ny/TY) x nz
+__host__ __device__ inline long long tile_count(const Geo &g, int TX, int TY)
+{
+    return (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY) * g.nz;
+}
+
+// ---- batches of independent float meshes (dg_batch_*) ----
+
+// Device descriptor of one instance of a batch.
+struct InstDev {
+    Geo g;
+    Ops<float> T;
+    float *Q, *Qt, *dQ;            // state, second state, RK register
+    double *dt;                    // this instance's time step (device)
+    unsigned long long *lam_bits;  // CFL maximum slot
+    int code;                      // N * 8 + tile variant
+};
+
+// One work item: one tile of one instance.
+struct BatchItem {
+    int inst;
+    int code;
+    long long tile;
+};
+
+// Host-side facts about a tile code (N * 8 + variant): tile shape, threads,
+// dynamic shared memory of the fused stage; false for an unknown code.
+bool tile_code_info(int code, int *tx, int *ty, int *threads, size_t *smem);
+
+// Launchers of the batched kernels (dg_kernels_f32.cu): one persistent launch
+// over all items; `threads` and `smem` cover the largest tile of the batch.
+// size class of a tile code (0: N <= 6, 256 threads; 1: N = 7, 352 threads)
+int batch_code_class(int code);
+int batch_class_threads(int cls);
+cudaError_t batch_stage(const BatchItem *items, int nitems, const InstDev *inst, int parity,
+                        float A, float B, int cls, int grid, size_t smem, cudaStream_t s);
+// parity 0: the current state is in Q, 1: in the second state Qt
+cudaError_t batch_cfl(const BatchItem *items, int nitems, const InstDev *inst, int ninst,
+                      int parity, double cfl, int *err, int grid, int threads, cudaStream_t s);
+int batch_stage_blocks_per_sm(int cls, size_t smem);
+
 // Launchers implemented per scalar type (dg_kernels_f64.cu / dg_kernels_f32.cu).
 // Each returns cudaSuccess or the launch error.
 template <typename real>

@@ -292,273 +292,7 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
     }
 }
 
-// ---------------------------------------------------------------------------
-// fused single-pass stage (float state): faces + volume + lift + update
-// ---------------------------------------------------------------------------
-//
-// For the float form the stage is bound by DRAM traffic and instruction
-// issue, not by a narrow pipe, so one kernel does all of it: a CTA stages its
-// elements' states and fluxes in shared memory, computes the Lax-Friedrichs
-// flux on all six faces of each of its elements (the neighbour's trace is
-// interpolated from the neighbour's face-normal node lines, read through L2,
-// or from shared memory when the neighbour is in the same CTA), then the
-// derivative, lift and update.  Each interface flux is evaluated by both
-// adjacent CTAs from bitwise-identical inputs in the same operation order, so
-// both see the same value and discrete conservation holds as in the
-// two-kernel form.  DRAM traffic per stage is Q read, dQ read/written and Q'
-// written: the output goes to a second state buffer, because neighbouring
-// CTAs still read the input state.
-
-// single-instruction float approximations (PTX rcp.approx / sqrt.approx,
-// relative error of order 2^-23, the float form's own rounding level)
-__device__ __forceinline__ float fast_rcp(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ float fast_sqrt(float x)
-{
-    float r;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-template <int DIR>
-__device__ __forceinline__ void normal_flux_f(const float q[NF], float gamma, float gm1,
-                                              float f[NF], float &speed)
-{
-    const float rinv = fast_rcp(q[0]);
-    const float mm = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-    const float p = gm1 * (q[4] - 0.5f * mm * rinv);
-    const float mn = q[1 + DIR];
-    const float un = mn * rinv;
-    f[0] = mn;
-    f[1] = q[1] * un + (DIR == 0 ? p : 0.0f);
-    f[2] = q[2] * un + (DIR == 1 ? p : 0.0f);
-    f[3] = q[3] * un + (DIR == 2 ? p : 0.0f);
-    f[4] = (q[4] + p) * un;
-    speed = fabsf(un) + fast_sqrt(gamma * p * rinv);
-}
-
-// N consecutive floats; vector loads when the line is 8- or 16-byte aligned
-// (N even: every line starts at a multiple of N floats from an aligned base)
-template <int N>
-__device__ __forceinline__ void load_line(const float *p, float v[N])
-{
-    if constexpr (N % 4 == 0) {
-#pragma unroll
-        for (int a = 0; a < N; a += 4) {
-            const float4 t = *reinterpret_cast<const float4 *>(p + a);
-            v[a] = t.x; v[a + 1] = t.y; v[a + 2] = t.z; v[a + 3] = t.w;
-        }
-    } else if constexpr (N % 2 == 0) {
-#pragma unroll
-        for (int a = 0; a < N; a += 2) {
-            const float2 t = *reinterpret_cast<const float2 *>(p + a);
-            v[a] = t.x; v[a + 1] = t.y;
-        }
-    } else {
-#pragma unroll
-        for (int a = 0; a < N; ++a) v[a] = p[a];
-    }
-}
-
-// Trace of an element on a face in direction DIR at node line (t1, t2):
-// sum_c l[c] Q(node c along DIR), from `src` (the element's field planes at
-// plane stride `pstride`); the same arithmetic for shared and global sources.
-template <int N, int DIR>
-__device__ __forceinline__ void line_trace(const float *src, long long pstride, int base,
-                                           const float *l, float q[NF])
-{
-    constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? N : N * N);
-#pragma unroll
-    for (int n = 0; n < NF; ++n) {
-        float v[N];
-        if constexpr (DIR == 0) {
-            load_line<N>(src + n * pstride + base, v);
-        } else {
-#pragma unroll
-            for (int c = 0; c < N; ++c) v[c] = src[n * pstride + base + c * stride];
-        }
-        float s = 0.0f;
-#pragma unroll
-        for (int c = 0; c < N; ++c) s += l[c] * v[c];
-        q[n] = s;
-    }
-}
-
-template <int N>
-struct FusedTile {
-    static constexpr int N2 = N * N, N3 = N * N * N;
-    static constexpr int EPB = Tile<N>::EPB, THREADS = Tile<N>::THREADS;
-    // face tasks: six faces, each a warp-aligned segment of EPB N^2 points
-    static constexpr int SEGF = ((EPB * N2 + 31) / 32) * 32;
-    // per-element strides in shared memory, padded to 16 (mod 32) floats so
-    // that two elements touched by one warp fall into different bank halves
-    static constexpr int pad16(int x) { return x + ((16 - x % 32) + 32) % 32; }
-    static constexpr int FSTR = pad16(3 * NF * N3);  // fluxes [3][NF][N3], direction-major nodes
-    static constexpr int QSTR = pad16(NF * N3);      // state [NF][N3]
-    static constexpr int HSTR = pad16(3 * NF * N2 * 2);  // face fluxes [3][NF][N2][2]: (-, +) pair
-    // shared memory: fluxes, state, face fluxes (floats), then the neighbour
-    // table [EPB][6] (long long)
-    static constexpr size_t FLOATS = (size_t)EPB * (FSTR + QSTR + HSTR);
-    static constexpr size_t BYTES = ((FLOATS * sizeof(float) + 15) / 16) * 16 + EPB * 6 * 8;
-    // resident CTAs per SM requested from the register allocator
-    static constexpr int MINB = THREADS <= 256 ? 5 : (THREADS <= 512 ? 2 : 1);
-};
-
-template <int N, int DIR>
-__device__ __forceinline__ void fused_face(const float *__restrict__ Qin, const float *sQ,
-                                           float *sH, const long long *sNb, const Ops<float> &T,
-                                           long long E, long long e0, int el, int side, int pt)
-{
-    constexpr int N2 = N * N, N3 = N * N * N, EPB = Tile<N>::EPB;
-    const int t1 = pt % N, t2 = pt / N;
-    const int base = DIR == 0 ? (t2 * N + t1) * N : (DIR == 1 ? t2 * N2 + t1 : t2 * N + t1);
-    const long long en = sNb[el * 6 + 2 * DIR + side];
-    // own trace at the face's end of the element, the neighbour's at the other end
-    float qo[NF], qn[NF];
-    constexpr int QSTR = FusedTile<N>::QSTR;
-    line_trace<N, DIR>(sQ + (size_t)el * QSTR, N3, base, side ? T.lp : T.lm, qo);
-    const long long rel = en - e0;
-    if (rel >= 0 && rel < EPB)
-        line_trace<N, DIR>(sQ + (size_t)rel * QSTR, N3, base, side ? T.lm : T.lp, qn);
-    else
-        line_trace<N, DIR>(Qin + en * N3, E * N3, base, side ? T.lm : T.lp, qn);
-    float fL[NF], fR[NF], sL, sR;
-    normal_flux_f<DIR>(side ? qo : qn, T.gamma, T.gm1, fL, sL);
-    normal_flux_f<DIR>(side ? qn : qo, T.gamma, T.gm1, fR, sR);
-    const float lam = fmaxf(sL, sR);
-    const float *qL = side ? qo : qn;
-    const float *qR = side ? qn : qo;
-    // (-, +) pair of the direction's two faces at this face point
-    float *h = sH + (size_t)el * FusedTile<N>::HSTR + (DIR * NF * N2 + pt) * 2 + side;
-#pragma unroll
-    for (int n = 0; n < NF; ++n) h[n * N2 * 2] = (fL[n] + fR[n]) - lam * (qR[n] - qL[n]);
-}
-
-template <int N, int MODE>
-__global__ void __launch_bounds__(Tile<N>::THREADS, FusedTile<N>::MINB)
-    fused_stage_kernel(const float *__restrict__ Qin, float *__restrict__ Out,
-                       float *__restrict__ dQ, const Ops<float> T, const Geo g, float A, float B,
-                       const double *__restrict__ dt)
-{
-    using FT = FusedTile<N>;
-    constexpr int N2 = FT::N2, N3 = FT::N3, EPB = FT::EPB, THREADS = FT::THREADS;
-    constexpr int SEGF = FT::SEGF, FSTR = FT::FSTR, QSTR = FT::QSTR, HSTR = FT::HSTR;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *sF = reinterpret_cast<float *>(smem_raw);  // [EPB][FSTR]: [3][NF][N3]
-    float *sQ = sF + EPB * FSTR;                      // [EPB][QSTR]: [NF][N3]
-    float *sH = sQ + EPB * QSTR;                      // [EPB][HSTR]: [3][NF][N2][2] (2 F*)
-    long long *sNb = reinterpret_cast<long long *>(smem_raw + (FT::BYTES - EPB * 6 * 8));
-
-    const int tid = threadIdx.x;
-    const int el = tid / N3;
-    const int node = tid - el * N3;
-    const long long e0 = (long long)blockIdx.x * EPB;
-    const long long e = e0 + el;
-    const bool active = el < EPB && e < g.E;
-    const int i = node % N, j = (node / N) % N, k = node / N2;
-
-    if (tid < EPB * 6) {  // the six neighbours of every element of the tile
-        const int te = tid / 6, f = tid - te * 6;
-        const long long ee = e0 + te;
-        long long nb = 0;
-        if (ee < g.E) {
-            const int side = (f & 1) ? +1 : -1;
-            nb = (f >> 1) == 0 ? neighbour<0>(ee, side, g)
-               : (f >> 1) == 1 ? neighbour<1>(ee, side, g) : neighbour<2>(ee, side, g);
-        }
-        sNb[tid] = nb;
-    }
-
-    float q[NF];
-    if (active) {
-#pragma unroll
-        for (int n = 0; n < NF; ++n) {
-            q[n] = Qin[sidx(n, e, node, g.E, N3)];
-            sQ[el * QSTR + n * N3 + node] = q[n];
-        }
-        const float rinv = fast_rcp(q[0]);
-        const float u = q[1] * rinv, v = q[2] * rinv, w = q[3] * rinv;
-        const float p = T.gm1 * (q[4] - 0.5f * (q[1] * u + q[2] * v + q[3] * w));
-        const float ep = q[4] + p;
-        // direction-major node order: the line a contraction reads is contiguous
-        float *sx = sF + (size_t)el * FSTR + 0 * NF * N3 + (k * N + j) * N + i;
-        float *sy = sF + (size_t)el * FSTR + 1 * NF * N3 + (k * N + i) * N + j;
-        float *sz = sF + (size_t)el * FSTR + 2 * NF * N3 + (j * N + i) * N + k;
-        sx[0 * N3] = q[1];
-        sx[1 * N3] = q[1] * u + p;
-        sx[2 * N3] = q[2] * u;
-        sx[3 * N3] = q[3] * u;
-        sx[4 * N3] = ep * u;
-        sy[0 * N3] = q[2];
-        sy[1 * N3] = q[1] * v;
-        sy[2 * N3] = q[2] * v + p;
-        sy[3 * N3] = q[3] * v;
-        sy[4 * N3] = ep * v;
-        sz[0 * N3] = q[3];
-        sz[1 * N3] = q[1] * w;
-        sz[2 * N3] = q[2] * w;
-        sz[3 * N3] = q[3] * w + p;
-        sz[4 * N3] = ep * w;
-    }
-    __syncthreads();
-
-    // the six faces of every element of the tile, face-major so that a warp
-    // works on one (direction, side)
-    for (int t = tid; t < 6 * SEGF; t += THREADS) {
-        const int face = t / SEGF;
-        const int r = t - face * SEGF;
-        if (r >= EPB * N2) continue;
-        const int el2 = r / N2;
-        const int pt = r - el2 * N2;
-        if (e0 + el2 >= g.E) continue;
-        const int side = face & 1;
-        if (face < 2) fused_face<N, 0>(Qin, sQ, sH, sNb, T, g.E, e0, el2, side, pt);
-        else if (face < 4) fused_face<N, 1>(Qin, sQ, sH, sNb, T, g.E, e0, el2, side, pt);
-        else fused_face<N, 2>(Qin, sQ, sH, sNb, T, g.E, e0, el2, side, pt);
-    }
-    __syncthreads();
-    if (!active) return;
-
-    const int px = k * N + j, py = k * N + i, pz = j * N + i;
-    float dtr = 0.0f;
-    if (MODE == 1) dtr = (float)(*dt);
-    const float *h = sH + (size_t)el * HSTR;
-    const float *f = sF + (size_t)el * FSTR;
-#pragma unroll
-    for (int n = 0; n < NF; ++n) {
-        float vx[N], vy[N], vz[N];
-        load_line<N>(f + 0 * NF * N3 + n * N3 + (k * N + j) * N, vx);
-        load_line<N>(f + 1 * NF * N3 + n * N3 + (k * N + i) * N, vy);
-        load_line<N>(f + 2 * NF * N3 + n * N3 + (j * N + i) * N, vz);
-        float acc = 0.0f;
-#pragma unroll
-        for (int a = 0; a < N; ++a) acc += T.D[0][i][a] * vx[a];
-#pragma unroll
-        for (int b = 0; b < N; ++b) acc += T.D[1][j][b] * vy[b];
-#pragma unroll
-        for (int c = 0; c < N; ++c) acc += T.D[2][k][c] * vz[c];
-        // lift: one (-, +) pair of face fluxes per direction
-        const float2 hx = *reinterpret_cast<const float2 *>(h + ((0 * NF + n) * N2 + px) * 2);
-        const float2 hy = *reinterpret_cast<const float2 *>(h + ((1 * NF + n) * N2 + py) * 2);
-        const float2 hz = *reinterpret_cast<const float2 *>(h + ((2 * NF + n) * N2 + pz) * 2);
-        acc += T.Lm[0][i] * hx.x - T.Lp[0][i] * hx.y;
-        acc += T.Lm[1][j] * hy.x - T.Lp[1][j] * hy.y;
-        acc += T.Lm[2][k] * hz.x - T.Lp[2][k] * hz.y;
-
-        const long long o = sidx(n, e, node, g.E, N3);
-        if (MODE == 0) {
-            Out[o] = acc;
-        } else {
-            const float d = (A == 0.0f ? 0.0f : A * dQ[o]) + dtr * acc;
-            dQ[o] = d;
-            Out[o] = q[n] + B * d;
-        }
-    }
-}
+#include "dg_fused.cuh"
 
 // ---------------------------------------------------------------------------
 // time step, integrals, initial states
@@ -872,25 +606,40 @@ cudaError_t launch_volume(const Geo &g, const Ops<real> &T, const real *Qin, rea
     return cudaGetLastError();
 }
 
+template <int N, int V, int MODE>
+cudaError_t launch_fused_v(const Geo &g, const Ops<float> &T, const float *Qin, float *Out,
+                           float *dQ, float A, float B, const double *dt, Prof *prof,
+                           cudaStream_t s)
+{
+    using SH = TileShape<N, V>;
+    using FT = FusedTile<N, SH::TX, SH::TY>;
+    const size_t smem = FT::BYTES;
+    if (smem > 48 * 1024) {
+        cudaError_t err = cudaFuncSetAttribute(fused_stage_kernel<N, V, MODE>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+        if (err != cudaSuccess) return err;
+    }
+    const long long blocks = tile_count(g, SH::TX, SH::TY);
+    if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
+    ProfScope ps(prof, kKindStage, s);
+    fused_stage_kernel<N, V, MODE><<<(unsigned)blocks, FT::THREADS, smem, s>>>(Qin, Out, dQ, T, g,
+                                                                                A, B, dt);
+    return cudaGetLastError();
+}
+
+// the tile variant of order N selected for the single-mesh path (tuning table)
 template <int N, int MODE>
 cudaError_t launch_fused(const Geo &g, const Ops<float> &T, const float *Qin, float *Out,
                          float *dQ, float A, float B, const double *dt, Prof *prof,
                          cudaStream_t s)
 {
-    using FT = FusedTile<N>;
-    const size_t smem = FT::BYTES;
-    if (smem > 48 * 1024) {
-        cudaError_t err = cudaFuncSetAttribute(fused_stage_kernel<N, MODE>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
-        if (err != cudaSuccess) return err;
-    }
-    const long long blocks = (g.E + FT::EPB - 1) / FT::EPB;
-    if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
-    ProfScope ps(prof, kKindStage, s);
-    fused_stage_kernel<N, MODE><<<(unsigned)blocks, FT::THREADS, smem, s>>>(Qin, Out, dQ, T, g, A,
-                                                                             B, dt);
-    return cudaGetLastError();
+    const int v = tile_variant(N);
+    if constexpr (kTileVariants[N] > 2)
+        if (v == 2) return launch_fused_v<N, (kTileVariants[N] > 2 ? 2 : 0), MODE>(g, T, Qin, Out, dQ, A, B, dt, prof, s);
+    if constexpr (kTileVariants[N] > 1)
+        if (v == 1) return launch_fused_v<N, (kTileVariants[N] > 1 ? 1 : 0), MODE>(g, T, Qin, Out, dQ, A, B, dt, prof, s);
+    return launch_fused_v<N, 0, MODE>(g, T, Qin, Out, dQ, A, B, dt, prof, s);
 }
 
 // The float form runs the fused single-pass stage (DRAM bound: one read of

@@ -66,6 +66,43 @@ _lib.dg_rhs_static.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double] * 7 + [
     ctypes.c_int, _vp, _vp, _vp]
 _lib.dg_rhs_static.restype = ctypes.c_int
 
+_lib.dg_tile_variant_count.argtypes = [ctypes.c_int]
+_lib.dg_tile_variant_count.restype = ctypes.c_int
+_lib.dg_tile_shape.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int)]
+_lib.dg_tile_shape.restype = ctypes.c_int
+_lib.dg_set_tile_variant.argtypes = [ctypes.c_int, ctypes.c_int]
+_lib.dg_set_tile_variant.restype = ctypes.c_int
+_lib.dg_get_tile_variant.argtypes = [ctypes.c_int]
+_lib.dg_get_tile_variant.restype = ctypes.c_int
+
+
+class DgInstance(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("p", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
+                ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("Q", ctypes.c_void_p), ("dQ", ctypes.c_void_p),
+                ("Qt", ctypes.c_void_p)]
+
+
+_lib.dg_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(DgInstance), ctypes.POINTER(_vp)]
+_lib.dg_batch_create.restype = ctypes.c_int
+_lib.dg_batch_destroy.argtypes = [_vp]
+_lib.dg_batch_destroy.restype = None
+_lib.dg_batch_sizes.argtypes = [_vp, _i64p, _i64p]
+_lib.dg_batch_sizes.restype = ctypes.c_int
+_lib.dg_batch_state_init.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _vp]
+_lib.dg_batch_state_init.restype = ctypes.c_int
+_lib.dg_batch_step.argtypes = [_vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp]
+_lib.dg_batch_step.restype = ctypes.c_int
+_lib.dg_batch_dt.argtypes = [_vp, _dp]
+_lib.dg_batch_dt.restype = ctypes.c_int
+_lib.dg_batch_norms.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
+_lib.dg_batch_norms.restype = ctypes.c_int
+_lib.dg_batch_last_error.argtypes = [_vp]
+_lib.dg_batch_last_error.restype = ctypes.c_int
+
 DG_PROFILE_KINDS = 7
 KERNEL_KINDS = ("face", "volume", "cfl", "norms", "init", "stage", "copy")
 DG_ERR_TOO_LARGE = 8
@@ -235,3 +272,121 @@ class Mesh:
     def profile_end(self):
         """{kind: (summed device ms, launches)} since profile_begin."""
         return dg_profile_end(self.h)
+
+
+# --- tile-shape tuning table of the float form ------------------------------
+
+def dg_tile_variant_count(p):
+    return _lib.dg_tile_variant_count(p)
+
+
+def dg_tile_shape(p, variant):
+    tx, ty = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.dg_tile_shape(p, variant, ctypes.byref(tx), ctypes.byref(ty)), "dg_tile_shape")
+    return tx.value, ty.value
+
+
+def dg_set_tile_variant(p, variant):
+    _check(_lib.dg_set_tile_variant(p, variant), "dg_set_tile_variant")
+
+
+def dg_get_tile_variant(p):
+    return _lib.dg_get_tile_variant(p)
+
+
+TUNING_PATH = os.path.join(_HERE, "tuning", "fused_tiles.json")
+
+
+def load_tuning(path=None):
+    """Select the tile variant per degree from an autotuner table (JSON with a
+    "variant" entry per degree); returns the table, or None if absent."""
+    import json
+    path = path or TUNING_PATH
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        table = json.load(f)
+    for p, ent in table.get("degrees", {}).items():
+        v = int(ent["variant"])
+        if 0 <= v < dg_tile_variant_count(int(p)):
+            dg_set_tile_variant(int(p), v)
+    return table
+
+
+# --- batches of independent float meshes ------------------------------------
+
+def state_shape(spec):
+    """Shape (5, elements, N, N, N) of an instance's state."""
+    N = spec["p"] + 1
+    return (NF, spec["nx"] * spec["ny"] * spec["nz"], N, N, N)
+
+
+class Batch:
+    """Independent DG_FP32 meshes advanced together (dg_batch_*).
+
+    specs: list of dicts with nx, ny, nz, p and optionally x0..Lz, gamma, and
+    optionally the instance's float tensors "Q", "dQ", "Qt" (else allocated
+    here).  The tensors are caller-owned memory as far as the library is
+    concerned; this object keeps references to them."""
+
+    def __init__(self, specs, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.specs = [dict(s) for s in specs]
+        self.Q, self.dQ, self.Qt = [], [], []
+        arr = (DgInstance * len(specs))()
+        for i, s in enumerate(self.specs):
+            q = s.get("Q")
+            if q is None:
+                q = torch.empty(state_shape(s), dtype=torch.float32, device=self.device)
+            dq = s.get("dQ")
+            if dq is None:
+                dq = torch.zeros_like(q)
+            qt = s.get("Qt")
+            self.Q.append(q)
+            self.dQ.append(dq)
+            self.Qt.append(qt)
+            arr[i] = DgInstance(s["nx"], s["ny"], s["nz"], s["p"], s.get("x0", 0.0), s.get("y0", 0.0),
+                                s.get("z0", 0.0), s.get("Lx", 1.0), s.get("Ly", 1.0), s.get("Lz", 1.0),
+                                s.get("gamma", 1.4), q.data_ptr(), dq.data_ptr(),
+                                None if qt is None else qt.data_ptr())
+        h = _vp()
+        with torch.cuda.device(self.device):
+            _check(_lib.dg_batch_create(len(specs), arr, ctypes.byref(h)), "dg_batch_create")
+        self.h = h
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.dg_batch_sizes(h, ctypes.byref(a), ctypes.byref(b)), "dg_batch_sizes")
+        self.n_dof, self.n_items = a.value, b.value
+
+    def __len__(self):
+        return len(self.specs)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            _lib.dg_batch_destroy(h)
+            self.h = None
+
+    def init(self, idx, kind, params, stream=None):
+        kinds = {"uniform": DG_INIT_UNIFORM, "vortex": DG_INIT_VORTEX, "tgv": DG_INIT_TGV}
+        arr = (ctypes.c_double * len(params))(*[float(x) for x in params])
+        _check(_lib.dg_batch_state_init(self.h, idx, kinds.get(kind, kind), arr, len(params),
+                                        _stream(stream)), "dg_batch_state_init")
+
+    def step(self, cfl, nsteps=1, use_graph=True, stream=None):
+        """Advance every instance by nsteps LSERK45 steps (each with its own CFL dt)."""
+        _check(_lib.dg_batch_step(self.h, float(cfl), int(nsteps), 1 if use_graph else 0,
+                                  _stream(stream)), "dg_batch_step")
+
+    def dts(self):
+        out = (ctypes.c_double * len(self.specs))()
+        _check(_lib.dg_batch_dt(self.h, out), "dg_batch_dt")
+        return list(out)
+
+    def norms(self, idx, Qref=None, out=None, stream=None):
+        out = torch.empty(DG_NORMS_LEN, dtype=torch.float64, device=self.device) if out is None else out
+        _check(_lib.dg_batch_norms(self.h, idx, _ptr(Qref), _ptr(out), _stream(stream)),
+               "dg_batch_norms")
+        return out
+
+    def last_error(self):
+        return _lib.dg_batch_last_error(self.h)

@@ -1,0 +1,158 @@
+"""Tile variants of the float form's fused stage, and batches of independent
+float meshes (one persistent launch per RK stage, optional CUDA graph).
+
+* every tile variant of every degree gives the oracle's right-hand side
+  (FP32 tolerance), also on meshes that tiles cover raggedly;
+* an instance advanced inside a batch equals the same instance advanced
+  alone, bitwise (same tile code, same arithmetic), and its time step equals
+  dg_cfl_dt's;
+* graph-replayed steps equal directly launched steps bitwise.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import dg_module, rhs_scale, to_dev, to_host
+from paper_2006_15698_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+BOX = (0.0, 0.0, 0.0, 10.0, 10.0, 10.0)
+
+
+@pytest.fixture
+def dgm():
+    dg = dg_module()
+    saved = {p: dg.dg_get_tile_variant(p) for p in range(0, 7)}
+    yield dg
+    for p, v in saved.items():
+        dg.dg_set_tile_variant(p, v)
+
+
+@pytest.mark.parametrize("p", range(0, 7))
+def test_every_tile_variant_matches_oracle(dgm, p):
+    dg = dgm
+    import torch
+    nel = (5, 7, 3)  # ragged against every tile shape
+    om = oracle.Mesh(*nel, p, *BOX)
+    prm = inputs.vortex_params(p, BOX)
+    prm[0] = 1.0 + 0.25 * (prm[0] - 1.0)
+    Q = om.init("vortex", prm).astype(np.float32).astype(np.float64)
+    R_or = om.rhs(Q)
+    for v in range(dg.dg_tile_variant_count(p)):
+        dg.dg_set_tile_variant(p, v)
+        m = dg.Mesh(*nel, p, *BOX, precision=dg.DG_FP32)
+        R = to_host(m.rhs(to_dev(Q, torch.float32)))
+        err = np.linalg.norm(R - R_or) / rhs_scale(om, Q)
+        assert err < 2e-6, (v, dg.dg_tile_shape(p, v), err)
+
+
+def _specs(seed, n):
+    r = inputs.uniforms(seed, 2 * n)
+    specs = []
+    for i in range(n):
+        ne = 3 + int(r[2 * i] * 6)      # 3..8 elements per side
+        p = 1 + int(r[2 * i + 1] * 5)   # 1..5
+        specs.append(dict(nx=ne, ny=ne + 1, nz=ne, p=p, Lx=10.0, Ly=10.0, Lz=10.0))
+    return specs
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_matches_single_meshes(dgm, use_graph):
+    dg = dgm
+    import torch
+    specs = _specs(11, 7)
+    batch = dg.Batch(specs)
+    for i, s in enumerate(specs):
+        batch.init(i, "vortex", inputs.vortex_params(100 + i, BOX))
+    singles = []
+    for i, s in enumerate(specs):
+        m = dg.Mesh(s["nx"], s["ny"], s["nz"], s["p"], *BOX, precision=dg.DG_FP32)
+        Q = batch.Q[i].clone()
+        singles.append((m, Q, torch.zeros_like(Q), torch.zeros(1, dtype=torch.float64, device="cuda")))
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for step in range(3):
+            batch.step(0.5, use_graph=use_graph)
+            for m, Q, dQ, dt in singles:
+                m.cfl_dt(Q, 0.5, dt)
+                m.rk_step(Q, dQ, dt)
+    torch.cuda.synchronize()
+    dts = batch.dts()
+    for i, (m, Q, dQ, dt) in enumerate(singles):
+        assert dts[i] == float(dt.item()), i
+        assert torch.equal(batch.Q[i], Q), (i, specs[i])
+    assert batch.last_error() == dg.DG_OK
+
+
+def test_batch_instance_against_oracle(dgm):
+    # one instance of a mixed batch after one step, against the FP64 oracle
+    dg = dgm
+    import torch
+    specs = [dict(nx=4, ny=3, nz=2, p=3, Lx=10.0, Ly=10.0, Lz=10.0),
+             dict(nx=5, ny=5, nz=5, p=1, Lx=10.0, Ly=10.0, Lz=10.0)]
+    om = oracle.Mesh(4, 3, 2, 3, *BOX)
+    Q0 = om.init("vortex", inputs.vortex_params(8, BOX)).astype(np.float32).astype(np.float64)
+    batch = dg.Batch(specs)
+    batch.Q[0].copy_(to_dev(Q0, torch.float32))
+    batch.init(1, "tgv", inputs.tgv_params(0.1))
+    batch.step(0.5, use_graph=False)
+    dt = batch.dts()[0]
+    Q1, _ = om.rk_steps(Q0, dt, 1)
+    err = np.linalg.norm(to_host(batch.Q[0]) - Q1) / np.linalg.norm(Q1)
+    assert err < 2e-7, err
+    out = to_host(batch.norms(0))
+    assert abs(out[0] - om.norms(Q1)[0]) < 1e-6 * abs(out[0])
+
+
+def test_batch_graph_equals_direct(dgm):
+    dg = dgm
+    import torch
+    specs = _specs(5, 5)
+    a, b = dg.Batch(specs), dg.Batch(specs)
+    for i in range(len(specs)):
+        a.init(i, "vortex", inputs.vortex_params(i, BOX))
+        b.init(i, "vortex", inputs.vortex_params(i, BOX))
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(4):
+            a.step(0.4, use_graph=True)
+            b.step(0.4, use_graph=False)
+    torch.cuda.synchronize()
+    for i in range(len(specs)):
+        assert torch.equal(a.Q[i], b.Q[i])
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_multi_step_call(dgm, use_graph):
+    # nsteps in one call (two-step groups ending in Q without a copy, then a
+    # last single step with the copy) equals nsteps single-step calls
+    dg = dgm
+    import torch
+    specs = _specs(7, 4)
+    a, b = dg.Batch(specs), dg.Batch(specs)
+    for i in range(len(specs)):
+        a.init(i, "vortex", inputs.vortex_params(50 + i, BOX))
+        b.init(i, "vortex", inputs.vortex_params(50 + i, BOX))
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a.step(0.5, nsteps=5, use_graph=use_graph)
+        for _ in range(5):
+            b.step(0.5, nsteps=1, use_graph=use_graph)
+    torch.cuda.synchronize()
+    assert a.dts() == b.dts()
+    for i in range(len(specs)):
+        assert torch.equal(a.Q[i], b.Q[i])
+
+
+def test_batch_rejects_bad_specs(dgm):
+    dg = dgm
+    with pytest.raises(dg.DGError):
+        dg.Batch([dict(nx=2, ny=2, nz=2, p=7)])
+    with pytest.raises(dg.DGError):
+        dg.Batch([dict(nx=0, ny=2, nz=2, p=1)])
