@@ -40,7 +40,11 @@ struct Tile {
     static constexpr int N2 = N * N;
     static constexpr int N3 = N * N * N;
     // elements per CTA of volume_kernel: about 256 threads (one per node)
-    static constexpr int EPB = N3 >= 128 ? 1 : (N3 >= 64 ? 4 : (256 / N3));
+    // (p = 4: two elements, 250 threads, so that three CTAs of the FP64
+    // volume kernel fit an SM's registers)
+    static constexpr int EPB = N3 >= 128 ? 1 : (N3 >= 100 ? 2 : (N3 >= 64 ? 4 : (256 / N3)));
+    // operator tables staged per CTA: D[3][N][N], Lp[3][N], Lm[3][N]
+    static constexpr int OPS = 3 * N * N + 6 * N;
     static constexpr int THREADS = ((EPB * N3 + 31) / 32) * 32;
 };
 
@@ -215,6 +219,9 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
     constexpr int N2 = N * N, N3 = N * N * N, EPB = Tile<N>::EPB;
     extern __shared__ unsigned char smem_raw[];
     real *sF = reinterpret_cast<real *>(smem_raw);  // [EPB][3][NF][N3]
+    real *sD = sF + (size_t)EPB * 3 * NF * N3;        // [3][N][N]
+    real *sLp = sD + 3 * N2;                           // [3][N]
+    real *sLm = sLp + 3 * N;                           // [3][N]
 
     const int tid = threadIdx.x;
     const int el = tid / N3;
@@ -222,6 +229,15 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
     const long long e = (long long)blockIdx.x * EPB + el;
     const bool active = el < EPB && e < g.E;
     const int i = node % N, j = (node / N) % N, k = node / N2;
+
+    // the operators, scaled once per CTA by dt for the stage update (so the
+    // accumulated value is already dt * R) and by 1 for the rhs
+    for (int t = tid; t < Tile<N>::OPS; t += blockDim.x) {
+        const real sc = MODE == 1 ? real(*dt) : real(1);
+        if (t < 3 * N2) sD[t] = sc * (&T.D[0][0][0])[(t / N2) * NMAX * NMAX + ((t % N2) / N) * NMAX + t % N];
+        else if (t < 3 * N2 + 3 * N) { const int u = t - 3 * N2; sLp[u] = sc * T.Lp[u / N][u % N]; }
+        else { const int u = t - 3 * N2 - 3 * N; sLm[u] = sc * T.Lm[u / N][u % N]; }
+    }
 
     real q[NF];
     if (active) {
@@ -257,8 +273,7 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
     const long long eym = neighbour<1>(e, -1, g);
     const long long ezm = neighbour<2>(e, -1, g);
     const int px = k * N + j, py = k * N + i, pz = j * N + i;
-    real dtr = real(0);
-    if (MODE == 1) dtr = real(*dt);
+    const real *Dx = sD + 0 * N2 + i * N, *Dy = sD + 1 * N2 + j * N, *Dz = sD + 2 * N2 + k * N;
 
 #pragma unroll
     for (int n = 0; n < NF; ++n) {
@@ -268,24 +283,25 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
         real acc = real(0);
         // sum-factorised weak derivative along x, y, z
 #pragma unroll
-        for (int a = 0; a < N; ++a) acc += T.D[0][i][a] * sx[(k * N + j) * N + a];
+        for (int a = 0; a < N; ++a) acc += Dx[a] * sx[(k * N + j) * N + a];
 #pragma unroll
-        for (int b = 0; b < N; ++b) acc += T.D[1][j][b] * sy[(k * N + b) * N + i];
+        for (int b = 0; b < N; ++b) acc += Dy[b] * sy[(k * N + b) * N + i];
 #pragma unroll
-        for (int c = 0; c < N; ++c) acc += T.D[2][k][c] * sz[(c * N + j) * N + i];
+        for (int c = 0; c < N; ++c) acc += Dz[c] * sz[(c * N + j) * N + i];
         // lift of the six interface fluxes (outward normal -> sign)
-        acc -= T.Lp[0][i] * __ldg(F + fidx(0, n, e, px, g.E, N2));
-        acc += T.Lm[0][i] * __ldg(F + fidx(0, n, exm, px, g.E, N2));
-        acc -= T.Lp[1][j] * __ldg(F + fidx(1, n, e, py, g.E, N2));
-        acc += T.Lm[1][j] * __ldg(F + fidx(1, n, eym, py, g.E, N2));
-        acc -= T.Lp[2][k] * __ldg(F + fidx(2, n, e, pz, g.E, N2));
-        acc += T.Lm[2][k] * __ldg(F + fidx(2, n, ezm, pz, g.E, N2));
+        acc -= sLp[0 * N + i] * __ldg(F + fidx(0, n, e, px, g.E, N2));
+        acc += sLm[0 * N + i] * __ldg(F + fidx(0, n, exm, px, g.E, N2));
+        acc -= sLp[1 * N + j] * __ldg(F + fidx(1, n, e, py, g.E, N2));
+        acc += sLm[1 * N + j] * __ldg(F + fidx(1, n, eym, py, g.E, N2));
+        acc -= sLp[2 * N + k] * __ldg(F + fidx(2, n, e, pz, g.E, N2));
+        acc += sLm[2 * N + k] * __ldg(F + fidx(2, n, ezm, pz, g.E, N2));
 
         const long long o = sidx(n, e, node, g.E, N3);
         if (MODE == 0) {
             Out[o] = acc;
         } else {
-            const real d = (A == real(0) ? real(0) : A * dQ[o]) + dtr * acc;
+            // acc already carries dt (scaled operators)
+            const real d = A == real(0) ? acc : A * dQ[o] + acc;
             dQ[o] = d;
             Out[o] = q[n] + B * d;
         }
@@ -591,7 +607,7 @@ cudaError_t launch_volume(const Geo &g, const Ops<real> &T, const real *Qin, rea
                           cudaStream_t s)
 {
     constexpr int EPB = Tile<N>::EPB, THREADS = Tile<N>::THREADS, N3 = N * N * N;
-    const size_t smem = (size_t)EPB * 3 * NF * N3 * sizeof(real);
+    const size_t smem = ((size_t)EPB * 3 * NF * N3 + Tile<N>::OPS) * sizeof(real);
     if (smem > 48 * 1024) {  // opt in above the default dynamic shared-memory limit
         cudaError_t err = cudaFuncSetAttribute(volume_kernel<N, real, MODE>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
