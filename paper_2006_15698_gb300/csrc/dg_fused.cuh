@@ -135,8 +135,11 @@ struct FusedTile {
     static constexpr int FSTR = pad16(3 * NF * N3);      // fluxes [3][NF][N3], direction-major
     static constexpr int QSTR = pad16(NF * N3);          // state [NF][N3]
     static constexpr int HSTR = pad16(3 * NF * N2 * 2);  // face fluxes [3][NF][N2][(-,+)]
-    // fluxes, state, face fluxes (floats), then the neighbour table [EPB][6]
-    static constexpr size_t FLOATS = (size_t)EPB * (FSTR + QSTR + HSTR);
+    // operators D[3][N][N], Lm[3][N], Lp[3][N] (read by every thread at its own
+    // node index, so from shared memory rather than the constant bank)
+    static constexpr int OPSF = ((3 * N2 + 6 * N + 3) / 4) * 4;
+    // fluxes, state, face fluxes, operators (floats), then the neighbour table [EPB][6]
+    static constexpr size_t FLOATS = (size_t)EPB * (FSTR + QSTR + HSTR) + OPSF;
     static constexpr size_t BYTES = ((FLOATS * sizeof(float) + 15) / 16) * 16 + EPB * 6 * 8;
 };
 
@@ -198,6 +201,7 @@ __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float 
     float *sF = reinterpret_cast<float *>(smem);  // [EPB][FSTR]
     float *sQ = sF + EPB * FSTR;                  // [EPB][QSTR]
     float *sH = sQ + EPB * QSTR;                  // [EPB][HSTR]
+    float *sOp = sH + EPB * HSTR;                 // D[3][N][N], Lm[3][N], Lp[3][N]
     long long *sNb = reinterpret_cast<long long *>(smem + (FT::BYTES - EPB * 6 * 8));
 
     // tile -> element coordinates of its corner
@@ -233,6 +237,14 @@ __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float 
                 nb = (long long)cx + (long long)g.nx * (cy + (long long)g.ny * cz);
         }
         sNb[t] = nb;
+    }
+
+    for (int t = tid; t < 3 * N2 + 6 * N; t += nthr) {
+        float v;
+        if (t < 3 * N2) v = T.D[t / N2][(t % N2) / N][t % N];
+        else if (t < 3 * N2 + 3 * N) v = T.Lm[(t - 3 * N2) / N][(t - 3 * N2) % N];
+        else v = T.Lp[(t - 3 * N2 - 3 * N) / N][(t - 3 * N2 - 3 * N) % N];
+        sOp[t] = v;
     }
 
     float q[NF];
@@ -288,6 +300,13 @@ __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float 
         const int px = k * N + j, py = k * N + i, pz = j * N + i;
         const float *h = sH + (size_t)el * HSTR;
         const float *f = sF + (size_t)el * FSTR;
+        float dx[N], dy[N], dz[N];
+        load_line<N>(sOp + 0 * N2 + i * N, dx);
+        load_line<N>(sOp + 1 * N2 + j * N, dy);
+        load_line<N>(sOp + 2 * N2 + k * N, dz);
+        const float *lm = sOp + 3 * N2, *lp = lm + 3 * N;
+        const float lmx = lm[i], lmy = lm[N + j], lmz = lm[2 * N + k];
+        const float lpx = lp[i], lpy = lp[N + j], lpz = lp[2 * N + k];
 #pragma unroll
         for (int n = 0; n < NF; ++n) {
             float vx[N], vy[N], vz[N];
@@ -296,18 +315,18 @@ __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float 
             load_line<N>(f + 2 * NF * N3 + n * N3 + (j * N + i) * N, vz);
             float acc = 0.0f;
 #pragma unroll
-            for (int c = 0; c < N; ++c) acc += T.D[0][i][c] * vx[c];
+            for (int c = 0; c < N; ++c) acc += dx[c] * vx[c];
 #pragma unroll
-            for (int c = 0; c < N; ++c) acc += T.D[1][j][c] * vy[c];
+            for (int c = 0; c < N; ++c) acc += dy[c] * vy[c];
 #pragma unroll
-            for (int c = 0; c < N; ++c) acc += T.D[2][k][c] * vz[c];
+            for (int c = 0; c < N; ++c) acc += dz[c] * vz[c];
             // lift: one (-, +) pair of face fluxes per direction
             const float2 hx = *reinterpret_cast<const float2 *>(h + ((0 * NF + n) * N2 + px) * 2);
             const float2 hy = *reinterpret_cast<const float2 *>(h + ((1 * NF + n) * N2 + py) * 2);
             const float2 hz = *reinterpret_cast<const float2 *>(h + ((2 * NF + n) * N2 + pz) * 2);
-            acc += T.Lm[0][i] * hx.x - T.Lp[0][i] * hx.y;
-            acc += T.Lm[1][j] * hy.x - T.Lp[1][j] * hy.y;
-            acc += T.Lm[2][k] * hz.x - T.Lp[2][k] * hz.y;
+            acc += lmx * hx.x - lpx * hx.y;
+            acc += lmy * hy.x - lpy * hy.y;
+            acc += lmz * hz.x - lpz * hz.y;
 
             const long long o = sidx(n, e, node, g.E, N3);
             if (MODE == 0) {
@@ -323,8 +342,11 @@ __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float 
 }
 
 // one mesh: one tile per CTA
+// (at least 1280 resident threads per SM: the tile's phases are separated by
+// barriers, and other CTAs' warps fill the gaps)
 template <int N, int V, int MODE>
-__global__ void __launch_bounds__(FusedTile<N, TileShape<N, V>::TX, TileShape<N, V>::TY>::THREADS)
+__global__ void __launch_bounds__(FusedTile<N, TileShape<N, V>::TX, TileShape<N, V>::TY>::THREADS,
+                                  1280 / FusedTile<N, TileShape<N, V>::TX, TileShape<N, V>::TY>::THREADS)
     fused_stage_kernel(const float *__restrict__ Qin, float *__restrict__ Out,
                        float *__restrict__ dQ, const Ops<float> T, const Geo g, float A, float B,
                        const double *__restrict__ dt)

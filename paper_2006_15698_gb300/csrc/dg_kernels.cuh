@@ -351,9 +351,43 @@ __device__ __forceinline__ bool node_speed(float r, float mx, float my, float mz
     return true;
 }
 
+// Float estimate of a double node's wave-speed sum, used only to skip the
+// exact evaluation of nodes that cannot hold the maximum.  Returns true when
+// the estimate is within kSpeedTol relative of the exact speed: every input
+// inside [1e-9, 1e9] in magnitude (density) or below 1e9 (momenta, energy),
+// so nothing overflows or goes subnormal in float; p >= E/100, so the
+// cancellation E - |m|^2/(2 rho) costs at most a factor 100 (float relative
+// error of p below 3e-5 for gamma <= 5/3, of c below half that); and a speed
+// above 1e-20.  Any other node (including NaN, rho <= 0 or p <= 0) is
+// evaluated exactly.
+constexpr float kSpeedTol = 6e-5f;
+__device__ __forceinline__ bool node_speed_estimate(double r, double mx, double my, double mz,
+                                                    double E, float gamma, float &s)
+{
+    const float rf = (float)r, xf = (float)mx, yf = (float)my, zf = (float)mz, ef = (float)E;
+    const float rinv = fast_rcp(rf);
+    const float u = xf * rinv, v = yf * rinv, w = zf * rinv;
+    const float p = (gamma - 1.0f) * (ef - 0.5f * rf * (u * u + v * v + w * w));
+    const float c = fast_sqrt(gamma * p * rinv);
+    s = (fabsf(u) + c) + (fabsf(v) + c) + (fabsf(w) + c);
+    const float big = 1e9f;
+    return rf >= 1e-9f && rf <= big && fabsf(xf) <= big && fabsf(yf) <= big &&
+           fabsf(zf) <= big && fabsf(ef) <= big && p >= 0.01f * ef && s >= 1e-20f;
+}
+
 // Lambda = max over nodes of sum_d (|u_d| + c), reduced in double; a node with
 // rho <= 0, p <= 0 or NaN contributes a NaN whose bit pattern is above every
 // finite value, and raises the error flag.
+//
+// Double state: the exact speed (IEEE divisions and square root) costs about
+// fifty FP64-pipe instructions, so each warp first estimates its 32 nodes'
+// speeds in float and keeps R, the running maximum of its well-conditioned
+// estimates.  Only nodes whose estimate reaches R (1 - 8 kSpeedTol), and the
+// nodes without a trustworthy estimate, are evaluated exactly.  The node x
+// holding the exact maximum S is always among them: its estimate is at least
+// S (1 - tol) while R is at most S (1 + tol), and (1 - tol) >= (1 + tol)
+// (1 - 8 tol).  The result is therefore the same double as the full
+// evaluation, bit for bit.
 template <typename real>
 __global__ void __launch_bounds__(256) cfl_kernel(const real *__restrict__ Q, long long nodes,
                                                   double gamma, unsigned long long *lam_bits,
@@ -361,15 +395,46 @@ __global__ void __launch_bounds__(256) cfl_kernel(const real *__restrict__ Q, lo
 {
     double m = 0.0;
     bool bad = false;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nodes;
-         t += (long long)gridDim.x * blockDim.x) {
-        double s;
-        if (!node_speed(Q[t], Q[nodes + t], Q[2 * nodes + t], Q[3 * nodes + t], Q[4 * nodes + t],
-                        gamma, s)) {
-            bad = true;
-            continue;
+    if constexpr (std::is_same<real, double>::value) {
+        const float gf = (float)gamma;
+        const float keep = 1.0f - 8.0f * kSpeedTol;
+        const int lane = threadIdx.x & 31;
+        const long long stride = (long long)gridDim.x * blockDim.x;  // a multiple of 32
+        float R = 0.0f;
+        // whole warps walk the nodes together, so the shuffles stay convergent
+        for (long long tb = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); tb < nodes;
+             tb += stride) {
+            const long long t = tb + lane;
+            const bool in = t < nodes;
+            double r = 1.0, mx = 0.0, my = 0.0, mz = 0.0, E = 0.0;
+            float sf = 0.0f;
+            bool ok = false;
+            if (in) {
+                r = Q[t]; mx = Q[nodes + t]; my = Q[2 * nodes + t]; mz = Q[3 * nodes + t];
+                E = Q[4 * nodes + t];
+                ok = node_speed_estimate(r, mx, my, mz, E, gf, sf);
+            }
+            float wm = ok ? sf : 0.0f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+            R = fmaxf(R, wm);
+            if (in && (!ok || sf >= R * keep)) {
+                double s;
+                if (node_speed(r, mx, my, mz, E, gamma, s)) m = fmax(m, s);
+                else bad = true;
+            }
         }
-        m = fmax(m, s);
+    } else {
+        for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nodes;
+             t += (long long)gridDim.x * blockDim.x) {
+            double s;
+            if (!node_speed(Q[t], Q[nodes + t], Q[2 * nodes + t], Q[3 * nodes + t],
+                            Q[4 * nodes + t], gamma, s)) {
+                bad = true;
+                continue;
+            }
+            m = fmax(m, s);
+        }
     }
     if (bad) {
         atomicOr(err, 1);
@@ -403,10 +468,28 @@ static __global__ void cfl_finalize_kernel(unsigned long long *lam_bits, double 
 // Pass 1 of the integrals: block b sums a fixed contiguous range of nodes in a
 // fixed order (thread-strided, then a shared-memory tree), so the result does
 // not depend on scheduling.  Values: I_0..I_4, KE, |Q-Qref|^2, |Qref|^2.
-// Quadrature weight J w_i w_j w_k of every in-element node (by value, constant bank).
+// Quadrature weight J w_i w_j w_k of every in-element node (passed by value,
+// staged in shared memory by the kernel: threads index it by their own node).
 struct NodeWeights {
     double w[NMAX * NMAX * NMAX];
 };
+
+// Float state: a thread's sums of w q are kept as unevaluated float pairs
+// (hi + lo) with error-free transformations -- Knuth's TwoSum for the sums,
+// the fma residual for the products, the double weight split into two floats
+// -- so they carry about 48 bits without touching the FP64 pipe; each thread
+// converts its pairs to double once, and everything after is double.
+__device__ __forceinline__ void ff_accumulate(float &hi, float &lo, float wh, float wl, float x)
+{
+    // explicitly rounded operations: no contraction may merge them
+    const float p = __fmul_rn(wh, x);
+    const float e = fmaf(wh, x, -p);  // wh x - p, exactly
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));  // hi + p - s
+    hi = s;
+    lo += err + fmaf(wl, x, e);
+}
 
 template <typename real>
 __global__ void __launch_bounds__(256) norms_partial_kernel(const real *__restrict__ Q,
@@ -415,44 +498,57 @@ __global__ void __launch_bounds__(256) norms_partial_kernel(const real *__restri
                                                             double *partials)
 {
     __shared__ double red[8][256];
+    __shared__ double sw[NMAX * NMAX * NMAX];  // weights by node (thread-varying index)
+    __shared__ float swh[NMAX * NMAX * NMAX], swl[NMAX * NMAX * NMAX];
     const int N = g.p + 1, N3 = N * N * N;
+    for (int t = threadIdx.x; t < N3; t += blockDim.x) {
+        sw[t] = W.w[t];
+        swh[t] = (float)W.w[t];
+        swl[t] = (float)(W.w[t] - (double)swh[t]);
+    }
+    __syncthreads();
     const long long nodes = g.E * N3;
     const long long chunk = (nodes + gridDim.x - 1) / gridDim.x;
     const long long beg = (long long)blockIdx.x * chunk;
     const long long end = beg + chunk < nodes ? beg + chunk : nodes;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    float fh[6] = {0, 0, 0, 0, 0, 0}, fl[6] = {0, 0, 0, 0, 0, 0};
     // in-element node index of t, advanced by the stride without a division
     int node = (int)((beg + threadIdx.x) % N3);
     const int step = (int)(blockDim.x % N3);
     for (long long t = beg + threadIdx.x; t < end; t += blockDim.x) {
-        const double wq = W.w[node];
+        const int nd = node;
         node += step;
         if (node >= N3) node -= N3;
-        double q[NF];
         real qr[NF];
 #pragma unroll
-        for (int n = 0; n < NF; ++n) {
-            qr[n] = Q[n * nodes + t];
-            q[n] = (double)qr[n];
-        }
-#pragma unroll
-        for (int n = 0; n < NF; ++n) acc[n] += wq * q[n];
+        for (int n = 0; n < NF; ++n) qr[n] = Q[n * nodes + t];
         if constexpr (sizeof(real) == 4) {
-            // float state: the kinetic-energy density in float (the state's
-            // own precision), accumulated in double
+            const float wh = swh[nd], wl = swl[nd];
+#pragma unroll
+            for (int n = 0; n < NF; ++n) ff_accumulate(fh[n], fl[n], wh, wl, qr[n]);
+            // the kinetic-energy density in float (the state's own precision)
             const float ke = 0.5f * (qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]) * fast_rcp(qr[0]);
-            acc[5] += wq * (double)ke;
+            ff_accumulate(fh[5], fl[5], wh, wl, ke);
         } else {
-            acc[5] += wq * 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * recip(q[0]);
+            const double wq = sw[nd];
+#pragma unroll
+            for (int n = 0; n < NF; ++n) acc[n] += wq * qr[n];
+            acc[5] += wq * 0.5 * (qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]) * recip(qr[0]);
         }
         if (Qref) {
+            const double wq = sw[nd];
 #pragma unroll
             for (int n = 0; n < NF; ++n) {
-                const double r = (double)Qref[n * nodes + t];
-                acc[6] += wq * (q[n] - r) * (q[n] - r);
+                const double q = (double)qr[n], r = (double)Qref[n * nodes + t];
+                acc[6] += wq * (q - r) * (q - r);
                 acc[7] += wq * r * r;
             }
         }
+    }
+    if constexpr (sizeof(real) == 4) {
+#pragma unroll
+        for (int v = 0; v < 6; ++v) acc[v] = (double)fh[v] + (double)fl[v];
     }
 #pragma unroll
     for (int v = 0; v < 8; ++v) red[v][threadIdx.x] = acc[v];

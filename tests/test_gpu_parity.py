@@ -113,6 +113,56 @@ def test_cfl_dt_bitwise(kind, p):
     assert abs(dt32 - dt32_or) <= 1e-6 * dt32_or
 
 
+def _uniform(om, rho=1.0, u=(0.3, -0.2, 0.1), p=1.0):
+    return om.init("uniform", [rho, *u, p])
+
+
+@pytest.mark.parametrize("case", ["all_equal", "near_ties", "high_mach", "float_range",
+                                  "spike_first", "spike_last", "spike_middle"])
+def test_cfl_pruned_reduction_bitwise(case):
+    """The FP64 reduction evaluates only the nodes a float estimate cannot
+    exclude; the time step stays bitwise equal to the oracle's in the cases
+    that stress the estimate: every node tied, ties closer than float can
+    resolve, Mach-20 nodes (pressure cancelled in float), magnitudes outside
+    the estimate's range, and a single fastest node at either end or in the
+    middle of a mesh large enough for several grid-stride sweeps per warp."""
+    dg = dg_module()
+    big = case.startswith("spike")
+    om = oracle.Mesh(40, 40, 40, 2, *BOX10) if big else oracle.Mesh(5, 3, 2, 3, *BOX10)
+    Q = _uniform(om)
+    flat = Q.reshape(5, -1)
+    rng = np.random.default_rng(17)
+    nn = flat.shape[1]
+    if case == "all_equal":
+        pass                         # every node ties: all evaluated exactly
+    elif case == "near_ties":
+        idx = rng.choice(nn, nn // 3, replace=False)
+        flat[1, idx] *= 1.0 + 1e-9 * rng.random(idx.size)
+    elif case == "high_mach":
+        idx = rng.choice(nn, 7, replace=False)
+        flat[1, idx] = 40.0          # |u| = 40 against c = 1.18: p << E/100
+        flat[4, idx] = 2.5 + 0.5 * 40.0 ** 2
+    elif case == "float_range":
+        flat[0, 3] = 1e-12           # density below the estimate's range
+        flat[1, 3] = flat[2, 3] = flat[3, 3] = 0.0
+        flat[4, 3] = 2.5e-12
+        flat[4, 11] = 2e9            # energy above it: the fastest node
+    else:
+        # spread speeds (the estimate skips most nodes), one fastest node and
+        # a twin slower by less than the estimate resolves
+        flat = inputs.random_state(om.shape, 23).reshape(5, -1)
+        t = {"spike_first": 0, "spike_last": nn - 1, "spike_middle": nn // 2 + 5}[case]
+        t2 = (t + 12345) % nn
+        for node, f in ((t, 1.0), (t2, 1.0 - 1e-7)):
+            flat[:, node] = [1.0, 2.0 * f, 0.1, -0.1, 2.5 + 0.5 * (4.0 * f * f + 0.02)]
+    Q = flat.reshape(om.shape)
+    dt_or, _ = om.cfl_dt(Q, 0.5)
+    m = dg.Mesh(om.nx, om.ny, om.nz, om.p, *BOX10)
+    dt = float(to_host(m.cfl_dt(to_dev(Q), 0.5))[0])
+    assert m.last_error() == dg.DG_OK
+    assert dt == dt_or, (dt, dt_or)
+
+
 def test_cfl_flags_nonpositive_pressure():
     dg = dg_module()
     om = oracle.Mesh(3, 2, 2, 2, *BOX10)
