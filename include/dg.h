@@ -203,6 +203,22 @@ dg_status dg_tile_shape(int p, int variant, int *tx, int *ty);
 dg_status dg_set_tile_variant(int p, int variant);
 int dg_get_tile_variant(int p);
 
+/* Stage kernel of the DG_FP32 single-mesh path (an implementation choice,
+ * not in the paper), per degree in a process-wide table like the tile table
+ * above (same threading rule; batches always use tiles):
+ *   DG_STAGE_TILE    one CTA per tile of one z layer (the tile variant above);
+ *                    the neighbour's face-normal lines read through L2
+ *   DG_STAGE_COLUMN  one CTA per column of elements, walking up a chunk of z
+ *                    layers with the next layers prefetched into shared
+ *                    memory (cp.async); every z interface computed once
+ * Both give the same right-hand side up to float rounding order.
+ *   dg_set_stage_kernel  DG_ERR_UNSUPPORTED for p outside [0, DG_MAX_P],
+ *                        DG_ERR_ARG for an unknown kind
+ *   dg_get_stage_kernel  the kind (-1 if p unsupported); default DG_STAGE_COLUMN */
+enum { DG_STAGE_TILE = 0, DG_STAGE_COLUMN = 1 };
+dg_status dg_set_stage_kernel(int p, int kind);
+int dg_get_stage_kernel(int p);
+
 /* Batches: many independent DG_FP32 meshes advanced together (the paper
  * solves one mesh; batching uneven independent problems is an addition).
  * Each instance is a periodic box like a dg_mesh (same meaning of nx..gamma)

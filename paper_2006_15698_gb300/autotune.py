@@ -1,12 +1,14 @@
-"""Tile-shape autotuner of the float form's fused RK stage.
+"""Autotuner of the float form's RK stage: tile shapes and stage kernel.
 
 For every polynomial degree it times one LSERK45 step of a representative
 float mesh (isentropic vortex, about `target_dof` nodes) with each tile
-variant the library offers (dg_tile_variant_count / dg_tile_shape), picks the
-fastest, and writes the table that ``dg.load_tuning`` reads:
+variant the library offers (dg_tile_variant_count / dg_tile_shape) and with
+the column kernel, and writes the table that ``dg.load_tuning`` reads: the
+fastest tile variant (used by batches, and by single meshes when "kernel" is
+"tile") and the faster single-mesh kernel:
 
-    {"gpu": ..., "degrees": {"3": {"variant": 1, "tile": [2, 2],
-                                   "ms_per_step": {"0": 5.1, "1": 4.8}}, ...}}
+    {"gpu": ..., "degrees": {"3": {"variant": 1, "tile": [2, 2], "kernel": "column",
+                                   "ms_per_step": {"0": 5.1, "1": 4.8, "column": 4.1}}, ...}}
 
 Run on the GPU the library will serve:
     python -m paper_2006_15698_gb300.autotune [--out PATH] [--degrees 1,2,3]
@@ -22,9 +24,14 @@ from . import dg, inputs
 
 
 def time_variant(p, variant, target_dof=8e6, steps=6, warmup=2):
-    """Milliseconds per LSERK45 step (CFL + 5 fused stages) of a float vortex
-    mesh of about target_dof nodes at degree p with the given tile variant."""
-    dg.dg_set_tile_variant(p, variant)
+    """Milliseconds per LSERK45 step (CFL + 5 stages) of a float vortex mesh
+    of about target_dof nodes at degree p with the given tile variant, or
+    with the column kernel for variant "column"."""
+    if variant == "column":
+        dg.dg_set_stage_kernel(p, dg.DG_STAGE_COLUMN)
+    else:
+        dg.dg_set_stage_kernel(p, dg.DG_STAGE_TILE)
+        dg.dg_set_tile_variant(p, variant)
     N = p + 1
     n = max(4, int(round((target_dof / N ** 3) ** (1 / 3))))
     box = (0.0, 0.0, 0.0, 16.0, 16.0, 16.0)
@@ -52,9 +59,14 @@ def tune(degrees=(1, 2, 3, 4, 5, 6), target_dof=8e6, steps=6):
         nv = dg.dg_tile_variant_count(p)
         times = {v: time_variant(p, v, target_dof, steps) for v in range(nv)}
         best = min(times, key=times.get)
+        t_col = time_variant(p, "column", target_dof, steps)
+        kernel = "column" if t_col < times[best] else "tile"
         dg.dg_set_tile_variant(p, best)
+        dg.dg_set_stage_kernel(p, dg.DG_STAGE_COLUMN if kernel == "column" else dg.DG_STAGE_TILE)
+        ms = {str(v): t for v, t in times.items()}
+        ms["column"] = t_col
         table["degrees"][str(p)] = {"variant": best, "tile": list(dg.dg_tile_shape(p, best)),
-                                    "ms_per_step": {str(v): t for v, t in times.items()}}
+                                    "kernel": kernel, "ms_per_step": ms}
     return table
 
 

@@ -309,6 +309,7 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
 }
 
 #include "dg_fused.cuh"
+#include "dg_column.cuh"
 
 // ---------------------------------------------------------------------------
 // time step, integrals, initial states
@@ -754,7 +755,52 @@ cudaError_t launch_fused(const Geo &g, const Ops<float> &T, const float *Qin, fl
     return launch_fused_v<N, 0, MODE>(g, T, Qin, Out, dQ, A, B, dt, prof, s);
 }
 
-// The float form runs the fused single-pass stage (DRAM bound: one read of
+// Column kernel launch: the z range of every column is cut into chunks so
+// that the number of CTAs fills the GPU's resident slots in whole waves
+// (time ~ waves x (layers per chunk + the chunk's extra prologue layer)).
+template <int N, int MODE>
+cudaError_t launch_column(const Geo &g, const Ops<float> &T, const float *Qin, float *Out,
+                          float *dQ, float A, float B, const double *dt, Prof *prof,
+                          cudaStream_t s)
+{
+    using SH = ColShape<N, 0>;
+    using CT = ColTile<N, SH::TX, SH::TY>;
+    static int resident = 0;  // CTAs of this kernel resident on the device at once
+    if (CT::BYTES > 48 * 1024) {
+        cudaError_t err = cudaFuncSetAttribute(column_stage_kernel<N, 0, MODE>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)CT::BYTES);
+        if (err != cudaSuccess) return err;
+    }
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t err = cudaGetDevice(&dev);
+        if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (err == cudaSuccess)
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, column_stage_kernel<N, 0, MODE>, CT::THREADS, CT::BYTES);
+        if (err != cudaSuccess) return err;
+        resident = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const long long ncols =
+        (long long)((g.nx + SH::TX - 1) / SH::TX) * ((g.ny + SH::TY - 1) / SH::TY);
+    int best_zc = g.nz;
+    double best = -1.0;
+    for (int nch = 1; nch <= g.nz && nch <= 64; ++nch) {
+        const int zc = (g.nz + nch - 1) / nch;
+        const long long ctas = ncols * ((g.nz + zc - 1) / zc);
+        const double cost = (double)((ctas + resident - 1) / resident) * (zc + 1);
+        if (best < 0.0 || cost < best) { best = cost; best_zc = zc; }
+    }
+    const long long blocks = ncols * ((g.nz + best_zc - 1) / best_zc);
+    if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
+    ProfScope ps(prof, kKindStage, s);
+    column_stage_kernel<N, 0, MODE><<<(unsigned)blocks, CT::THREADS, CT::BYTES, s>>>(
+        Qin, Out, dQ, T, g, A, B, dt, best_zc);
+    return cudaGetLastError();
+}
+
+// The float form runs the single-pass column stage (DRAM bound: one read of
 // the state per stage); the double form the two-kernel stage (FP64-pipe
 // bound: every interface flux evaluated once).
 template <int N, typename real>
@@ -762,6 +808,8 @@ cudaError_t rhs_n(const Geo &g, const Ops<real> &T, const real *Q, real *R, Work
                   cudaStream_t s)
 {
     if constexpr (std::is_same<real, float>::value) {
+        if (column_stage(N))
+            return launch_column<N, 0>(g, T, Q, R, nullptr, 0.0f, 0.0f, nullptr, w.prof, s);
         return launch_fused<N, 0>(g, T, Q, R, nullptr, 0.0f, 0.0f, nullptr, w.prof, s);
     } else {
         real *F = static_cast<real *>(w.face_flux);
@@ -783,8 +831,12 @@ cudaError_t rk_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, const doub
         for (int st = 0; st < 5; ++st) {
             const real *src = (st % 2 == 0) ? Q : Tq;
             real *dst = (st % 2 == 0) ? Tq : Q;
-            cudaError_t err = launch_fused<N, 1>(g, T, src, dst, dQ, float(kRkA[st]),
-                                                 float(kRkB[st]), dt, w.prof, s);
+            cudaError_t err =
+                column_stage(N)
+                    ? launch_column<N, 1>(g, T, src, dst, dQ, float(kRkA[st]), float(kRkB[st]),
+                                          dt, w.prof, s)
+                    : launch_fused<N, 1>(g, T, src, dst, dQ, float(kRkA[st]), float(kRkB[st]),
+                                         dt, w.prof, s);
             if (err != cudaSuccess) return err;
         }
         const size_t bytes = (size_t)NF * (size_t)g.E * N * N * N * sizeof(real);

@@ -75,6 +75,10 @@ _lib.dg_set_tile_variant.argtypes = [ctypes.c_int, ctypes.c_int]
 _lib.dg_set_tile_variant.restype = ctypes.c_int
 _lib.dg_get_tile_variant.argtypes = [ctypes.c_int]
 _lib.dg_get_tile_variant.restype = ctypes.c_int
+_lib.dg_set_stage_kernel.argtypes = [ctypes.c_int, ctypes.c_int]
+_lib.dg_set_stage_kernel.restype = ctypes.c_int
+_lib.dg_get_stage_kernel.argtypes = [ctypes.c_int]
+_lib.dg_get_stage_kernel.restype = ctypes.c_int
 
 
 class DgInstance(ctypes.Structure):
@@ -294,12 +298,25 @@ def dg_get_tile_variant(p):
     return _lib.dg_get_tile_variant(p)
 
 
+DG_STAGE_TILE, DG_STAGE_COLUMN = 0, 1
+
+
+def dg_set_stage_kernel(p, kind):
+    _check(_lib.dg_set_stage_kernel(p, kind), "dg_set_stage_kernel")
+
+
+def dg_get_stage_kernel(p):
+    return _lib.dg_get_stage_kernel(p)
+
+
 TUNING_PATH = os.path.join(_HERE, "tuning", "fused_tiles.json")
 
 
 def load_tuning(path=None):
-    """Select the tile variant per degree from an autotuner table (JSON with a
-    "variant" entry per degree); returns the table, or None if absent."""
+    """Select the tile variant and the single-mesh stage kernel per degree
+    from an autotuner table (JSON with "variant" and optionally "kernel"
+    ("tile" or "column") entries per degree); returns the table, or None if
+    absent."""
     import json
     path = path or TUNING_PATH
     if not os.path.exists(path):
@@ -310,6 +327,9 @@ def load_tuning(path=None):
         v = int(ent["variant"])
         if 0 <= v < dg_tile_variant_count(int(p)):
             dg_set_tile_variant(int(p), v)
+        kind = ent.get("kernel")
+        if kind in ("tile", "column"):
+            dg_set_stage_kernel(int(p), DG_STAGE_COLUMN if kind == "column" else DG_STAGE_TILE)
     return table
 
 

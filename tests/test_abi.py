@@ -73,3 +73,24 @@ def test_null_handles_rejected(lib):
             assert f(*([None] * nargs)) == 1
     lib.dg_mesh_destroy.argtypes = [ctypes.c_void_p]
     lib.dg_mesh_destroy(None)  # NULL is ignored
+
+
+def test_tuning_tables_validate_on_host(lib):
+    """The process-wide tile-variant and stage-kernel tables: defaults,
+    round trips, and host-side rejection of bad degrees and kinds."""
+    lib.dg_set_stage_kernel.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.dg_get_stage_kernel.argtypes = [ctypes.c_int]
+    lib.dg_set_tile_variant.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.dg_get_tile_variant.argtypes = [ctypes.c_int]
+    lib.dg_tile_variant_count.argtypes = [ctypes.c_int]
+    for p in range(7):
+        assert lib.dg_get_stage_kernel(p) in (0, 1)
+        assert lib.dg_tile_variant_count(p) >= 1
+    assert lib.dg_get_stage_kernel(-1) == -1 and lib.dg_get_stage_kernel(7) == -1
+    assert lib.dg_set_stage_kernel(7, 0) == 2          # DG_ERR_UNSUPPORTED
+    assert lib.dg_set_stage_kernel(3, 5) == 1          # DG_ERR_ARG
+    saved = lib.dg_get_stage_kernel(3)
+    assert lib.dg_set_stage_kernel(3, 0) == 0 and lib.dg_get_stage_kernel(3) == 0
+    assert lib.dg_set_stage_kernel(3, 1) == 0 and lib.dg_get_stage_kernel(3) == 1
+    lib.dg_set_stage_kernel(3, saved)
+    assert lib.dg_set_tile_variant(3, lib.dg_tile_variant_count(3)) == 1

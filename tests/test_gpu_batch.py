@@ -1,5 +1,7 @@
 """Tile variants of the float form's fused stage, and batches of independent
 float meshes (one persistent launch per RK stage, optional CUDA graph).
+(Single meshes default to the column stage kernel; the tests that compare a
+single mesh with a batch bitwise select the tile kernel for it.)
 
 * every tile variant of every degree gives the oracle's right-hand side
   (FP32 tolerance), also on meshes that tiles cover raggedly;
@@ -25,10 +27,11 @@ BOX = (0.0, 0.0, 0.0, 10.0, 10.0, 10.0)
 @pytest.fixture
 def dgm():
     dg = dg_module()
-    saved = {p: dg.dg_get_tile_variant(p) for p in range(0, 7)}
+    saved = {p: (dg.dg_get_tile_variant(p), dg.dg_get_stage_kernel(p)) for p in range(0, 7)}
     yield dg
-    for p, v in saved.items():
+    for p, (v, k) in saved.items():
         dg.dg_set_tile_variant(p, v)
+        dg.dg_set_stage_kernel(p, k)
 
 
 @pytest.mark.parametrize("p", range(0, 7))
@@ -41,6 +44,7 @@ def test_every_tile_variant_matches_oracle(dgm, p):
     prm[0] = 1.0 + 0.25 * (prm[0] - 1.0)
     Q = om.init("vortex", prm).astype(np.float32).astype(np.float64)
     R_or = om.rhs(Q)
+    dg.dg_set_stage_kernel(p, dg.DG_STAGE_TILE)
     for v in range(dg.dg_tile_variant_count(p)):
         dg.dg_set_tile_variant(p, v)
         m = dg.Mesh(*nel, p, *BOX, precision=dg.DG_FP32)
@@ -63,6 +67,8 @@ def _specs(seed, n):
 def test_batch_matches_single_meshes(dgm, use_graph):
     dg = dgm
     import torch
+    for p in range(0, 7):  # single meshes on the batch's tile kernel: bitwise comparable
+        dg.dg_set_stage_kernel(p, dg.DG_STAGE_TILE)
     specs = _specs(11, 7)
     batch = dg.Batch(specs)
     for i, s in enumerate(specs):

@@ -76,3 +76,46 @@ def test_fp32_step_and_dt(p):
     ref = om.norms(to_host(Q))
     assert np.max(np.abs(out[:5] - ref[:5]) / np.maximum(np.abs(ref[:5]), 1)) < 1e-13
     assert abs(out[5] - ref[5]) < 1e-6 * abs(ref[5])
+
+
+# meshes for the column stage kernel: many z chunks per column (short columns
+# against the GPU's resident CTA count), ragged cross-sections, nz = 1 and 2
+# (the layer above/below is the layer itself or its only neighbour), and a
+# single column (the neighbour column is the column itself)
+COLUMN_MESHES = [((5, 7, 24), 3), ((3, 2, 1), 2), ((1, 1, 5), 4), ((4, 3, 2), 1),
+                 ((2, 3, 9), 5), ((2, 1, 3), 6), ((6, 5, 4), 0)]
+
+
+@pytest.mark.parametrize("nel,p", COLUMN_MESHES)
+def test_column_kernel_rhs_and_step(nel, p):
+    """The column stage kernel against the oracle (float tolerance) and
+    against the tile kernel (same arithmetic up to float rounding order)."""
+    dg = dg_module()
+    import torch
+    from gpu_helpers import rhs_scale
+    om = oracle.Mesh(*nel, p, *BOX16)
+    prm = inputs.vortex_params(7 + p, BOX16)
+    prm[0] = 1.0 + 0.25 * (prm[0] - 1.0)
+    Q0 = om.init("vortex", prm).astype(np.float32).astype(np.float64)
+    R_or = om.rhs(Q0)
+    saved = dg.dg_get_stage_kernel(p)
+    try:
+        out = {}
+        for kind in (dg.DG_STAGE_COLUMN, dg.DG_STAGE_TILE):
+            dg.dg_set_stage_kernel(p, kind)
+            m = dg.Mesh(*nel, p, *BOX16, precision=dg.DG_FP32)
+            R = to_host(m.rhs(to_dev(Q0, torch.float32)))
+            assert np.linalg.norm(R - R_or) / rhs_scale(om, Q0) < 2e-6, kind
+            Q = to_dev(Q0, torch.float32)
+            dQ = torch.zeros_like(Q)
+            dt = m.cfl_dt(Q, 0.5)
+            m.rk_step(Q, dQ, dt)
+            out[kind] = (R, to_host(Q))
+        dtv = float(om.cfl_dt(Q0, 0.5)[0])
+        Q1, _ = om.rk_steps(Q0, dtv, 1)
+        for kind, (R, Q) in out.items():
+            assert rel_l2(Q, Q1) < 2e-7, kind
+        assert rel_l2(out[dg.DG_STAGE_COLUMN][1], out[dg.DG_STAGE_TILE][1]) < 2e-7
+    finally:
+        dg.dg_set_stage_kernel(p, saved)
+
