@@ -101,38 +101,30 @@ __device__ __forceinline__ double recip(double x)
 }
 __device__ __forceinline__ float recip(float x) { return 1.0f / x; }
 
-// Normal flux F^DIR(q), its normal velocity magnitude + sound speed.
-template <int DIR, typename real>
-__device__ __forceinline__ void normal_flux(const real q[NF], real gamma, real gm1, real f[NF],
-                                           real &speed)
-{
-    const real rinv = recip(q[0]);
-    const real mm = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-    const real p = gm1 * (q[4] - real(0.5) * mm * rinv);
-    const real mn = q[1 + DIR];
-    const real un = mn * rinv;
-    f[0] = mn;
-    f[1] = q[1] * un + (DIR == 0 ? p : real(0));
-    f[2] = q[2] * un + (DIR == 1 ? p : real(0));
-    f[3] = q[3] * un + (DIR == 2 ? p : real(0));
-    f[4] = (q[4] + p) * un;
-    speed = fabs(un) + sqrt(gamma * p * rinv);
-}
-
 // Local Lax-Friedrichs (Rusanov) flux through a face with normal +e_DIR,
 // qL on the -side, qR on the +side (Sec. II.B; local dissipation speed):
 //   F* = (F(qL) + F(qR))/2 - max(|u_n| + c)/2 (qR - qL)
-// Returned as 2 F* (the factor 1/2 is folded into the lift vectors).
+// Returned as 2 F* (the factor 1/2 is folded into the lift vectors).  Each
+// side's 1/rho, pressure and normal velocity are formed first and every flux
+// component F(q)_n = q_n u_n (+ p) is evaluated where it is combined, so
+// fewer values are live at once (the kernel's occupancy is register bound).
 template <int DIR, typename real>
 __device__ __forceinline__ void lf_flux2(const real qL[NF], const real qR[NF], real gamma,
                                          real gm1, real f[NF])
 {
-    real fL[NF], fR[NF], sL, sR;
-    normal_flux<DIR>(qL, gamma, gm1, fL, sL);
-    normal_flux<DIR>(qR, gamma, gm1, fR, sR);
-    const real lam = fmax(sL, sR);
+    const real rL = recip(qL[0]), rR = recip(qR[0]);
+    const real pL = gm1 * (qL[4] - real(0.5) * (qL[1] * qL[1] + qL[2] * qL[2] + qL[3] * qL[3]) * rL);
+    const real pR = gm1 * (qR[4] - real(0.5) * (qR[1] * qR[1] + qR[2] * qR[2] + qR[3] * qR[3]) * rR);
+    const real uL = qL[1 + DIR] * rL, uR = qR[1 + DIR] * rR;
+    const real lam = fmax(fabs(uL) + sqrt(gamma * pL * rL), fabs(uR) + sqrt(gamma * pR * rR));
+    f[0] = (qL[1 + DIR] + qR[1 + DIR]) - lam * (qR[0] - qL[0]);
 #pragma unroll
-    for (int n = 0; n < NF; ++n) f[n] = (fL[n] + fR[n]) - lam * (qR[n] - qL[n]);
+    for (int n = 1; n < 4; ++n) {
+        const real fl = qL[n] * uL + (n == DIR + 1 ? pL : real(0));
+        const real fr = qR[n] * uR + (n == DIR + 1 ? pR : real(0));
+        f[n] = (fl + fr) - lam * (qR[n] - qL[n]);
+    }
+    f[4] = ((qL[4] + pL) * uL + (qR[4] + pR) * uR) - lam * (qR[4] - qL[4]);
 }
 
 // ---------------------------------------------------------------------------
@@ -188,7 +180,7 @@ struct FaceTile {
 };
 
 template <int N, typename real>
-__global__ void __launch_bounds__(FaceTile<N>::THREADS)
+__global__ void __launch_bounds__(FaceTile<N>::THREADS, 1152 / FaceTile<N>::THREADS)
     face_flux_kernel(const real *__restrict__ Q, real *__restrict__ F, const Ops<real> T,
                      const Geo g)
 {
