@@ -108,16 +108,17 @@ __device__ __forceinline__ int line_base(int t1, int t2)
     return DIR == 0 ? (t2 * N + t1) * N : (DIR == 1 ? t2 * N * N + t1 : t2 * N + t1);
 }
 
-// trace of an element of the neighbour column, from DRAM/L2
-template <int N, int DIR>
-__device__ __forceinline__ void global_trace(const float *__restrict__ Q, long long E, long long e,
-                                             int base, const float *l, float q[NF])
+// trace of an element of the neighbour column, from DRAM/L2 (Ix: the index
+// type of the mesh's arrays, 32-bit when every offset fits)
+template <int N, int DIR, typename Ix>
+__device__ __forceinline__ void global_trace(const float *__restrict__ Q, Ix E, Ix e, int base,
+                                             const float *l, float q[NF])
 {
     constexpr int N3 = N * N * N;
 #pragma unroll
     for (int n = 0; n < NF; ++n) {
         float v[N];
-        line_values<N, DIR>(Q + ((long long)n * E + e) * N3 + base, v);
+        line_values<N, DIR>(Q + ((Ix)n * E + e) * N3 + base, v);
         q[n] = line_dot<N>(l, v);
     }
 }
@@ -136,22 +137,22 @@ __device__ __forceinline__ void lf_flux2_f(const float qL[NF], const float qR[NF
 }
 
 // Copy layer zl (periodic) of the column into a slot: whole valid rows.
-template <int N, int TX, int TY>
+template <int N, int TX, int TY, typename Ix>
 __device__ __forceinline__ void column_prefetch(const float *__restrict__ Q, float *slot,
                                                 const Geo &g, int ex0, int ey0, int txv, int tyv,
                                                 int zl)
 {
     using CT = ColTile<N, TX, TY>;
     constexpr int N3 = CT::N3, W = CT::W, RU = CT::ROW_UNITS, EPB = CT::EPB;
-    const long long plane = (long long)g.nx * g.ny;
+    const Ix plane = (Ix)g.nx * g.ny;
     for (int t = threadIdx.x; t < NF * TY * RU; t += blockDim.x) {
         const int n = t / (TY * RU);
         const int r = t - n * (TY * RU);
         const int b = r / RU;
         const int u = r - b * RU;
         if (b >= tyv || u * W >= txv * N3) continue;
-        const long long e0 = ex0 + (long long)g.nx * (ey0 + b) + plane * zl;
-        const float *src = Q + ((long long)n * g.E + e0) * N3 + u * W;
+        const Ix e0 = ex0 + (Ix)g.nx * (ey0 + b) + plane * zl;
+        const float *src = Q + ((Ix)n * (Ix)g.E + e0) * N3 + u * W;
         float *dst = slot + (n * EPB + b * TX) * N3 + u * W;
         if constexpr (W == 4) cp_async16(dst, src);
         else cp_async4(dst, src);
@@ -182,12 +183,11 @@ __device__ __forceinline__ void line_task(const float *slot, float *sT, const fl
 // x (DIR 0) or y (DIR 1) interface task: interface a in [0, len] along DIR of
 // row r (the other in-plane index); a = 0 and a = len are the column's
 // boundaries, whose outer trace comes from the neighbour column.
-template <int N, int TX, int TY, int DIR>
+template <int N, int TX, int TY, int DIR, typename Ix>
 __device__ __forceinline__ void plane_interface(const float *__restrict__ Qin, const float *sT,
                                                 float *sH, const Geo &g, const float *lm,
                                                 const float *lp, float gamma, float gm1, int a,
-                                                int r, int len, long long e_lo, long long e_hi,
-                                                int pt)
+                                                int r, int len, Ix e_lo, Ix e_hi, int pt)
 {
     using CT = ColTile<N, TX, TY>;
     constexpr int N2 = CT::N2;
@@ -196,14 +196,14 @@ __device__ __forceinline__ void plane_interface(const float *__restrict__ Qin, c
     auto local = [&](int c) { return DIR == 0 ? r * TX + c : c * TX + r; };
     float qL[NF], qR[NF];
     if (a == 0) {
-        global_trace<N, DIR>(Qin, g.E, e_lo, line_base<N, DIR>(t1, t2), lp, qL);
+        global_trace<N, DIR, Ix>(Qin, (Ix)g.E, e_lo, line_base<N, DIR>(t1, t2), lp, qL);
     } else {
         const float *t = sT + (size_t)local(a - 1) * CT::TSTR + (2 * DIR + 1) * NF * N2 + pt;
 #pragma unroll
         for (int n = 0; n < NF; ++n) qL[n] = t[n * N2];
     }
     if (a == len) {
-        global_trace<N, DIR>(Qin, g.E, e_hi, line_base<N, DIR>(t1, t2), lm, qR);
+        global_trace<N, DIR, Ix>(Qin, (Ix)g.E, e_hi, line_base<N, DIR>(t1, t2), lm, qR);
     } else {
         const float *t = sT + (size_t)local(a) * CT::TSTR + (2 * DIR + 0) * NF * N2 + pt;
 #pragma unroll
@@ -224,9 +224,11 @@ __device__ __forceinline__ void plane_interface(const float *__restrict__ Qin, c
 }
 
 // One column chunk of the stage.  MODE 0 writes the rhs to Out, MODE 1 the
-// LSERK stage update (dQ <- A dQ + dt R, Out <- Qin + B dQ).
+// LSERK stage update (dQ <- A dQ + dt R, Out <- Qin + B dQ).  Ix is the index
+// type of the state arrays: int when 5 E N^3 fits (32-bit address arithmetic
+// is measurably cheaper here), else a 64-bit integer.
 // (shared memory holds about four CTAs per SM; registers are sized for that)
-template <int N, int V, int MODE>
+template <int N, int V, int MODE, typename Ix>
 __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>::TY>::THREADS,
                                   1024 / ColTile<N, ColShape<N, V>::TX, ColShape<N, V>::TY>::THREADS)
     column_stage_kernel(const float *__restrict__ Qin, float *__restrict__ Out,
@@ -269,7 +271,8 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
     // periodic neighbour columns (element coordinates of the halo rows)
     const int exL = (ex0 - 1 + g.nx) % g.nx, exR = (ex0 + txv) % g.nx;
     const int eyL = (ey0 - 1 + g.ny) % g.ny, eyR = (ey0 + tyv) % g.ny;
-    const long long plane = (long long)g.nx * g.ny;
+    const Ix plane = (Ix)g.nx * g.ny;
+    const Ix E = (Ix)g.E;
 
     // this thread's node
     const int el = tid / N3;
@@ -283,9 +286,9 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
     auto zmod = [&](int L) { return (L % g.nz + g.nz) % g.nz; };
 
     // prologue: layers z0 - 1, z0, z0 + 1; the z interface below z0
-    column_prefetch<N, TX, TY>(Qin, slot_of(z0 - 1), g, ex0, ey0, txv, tyv, zmod(z0 - 1));
-    column_prefetch<N, TX, TY>(Qin, slot_of(z0), g, ex0, ey0, txv, tyv, zmod(z0));
-    column_prefetch<N, TX, TY>(Qin, slot_of(z0 + 1), g, ex0, ey0, txv, tyv, zmod(z0 + 1));
+    column_prefetch<N, TX, TY, Ix>(Qin, slot_of(z0 - 1), g, ex0, ey0, txv, tyv, zmod(z0 - 1));
+    column_prefetch<N, TX, TY, Ix>(Qin, slot_of(z0), g, ex0, ey0, txv, tyv, zmod(z0));
+    column_prefetch<N, TX, TY, Ix>(Qin, slot_of(z0 + 1), g, ex0, ey0, txv, tyv, zmod(z0 + 1));
     cp_async_wait_all();
     __syncthreads();
     for (int t = tid; t < 2 * EPB * N2; t += nthr) {
@@ -313,18 +316,18 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
     }
     __syncthreads();
     if (z0 + 2 <= z1)
-        column_prefetch<N, TX, TY>(Qin, slot_of(z0 + 2), g, ex0, ey0, txv, tyv, zmod(z0 + 2));
+        column_prefetch<N, TX, TY, Ix>(Qin, slot_of(z0 + 2), g, ex0, ey0, txv, tyv, zmod(z0 + 2));
 
     for (int z = z0; z < z1; ++z) {
         const float *cur = slot_of(z), *nxt = slot_of(z + 1);
-        const long long e = ex0 + a + (long long)g.nx * (ey0 + b) + plane * z;
+        const Ix e = ex0 + a + (Ix)g.nx * (ey0 + b) + plane * z;
 
         // B: node fluxes, line traces; the node's dQ fetched early
         float dq[NF];
         if (active) {
             if (MODE == 1 && A != 0.0f) {
 #pragma unroll
-                for (int n = 0; n < NF; ++n) dq[n] = dQ[sidx(n, e, node, g.E, N3)];
+                for (int n = 0; n < NF; ++n) dq[n] = dQ[((Ix)n * E + e) * N3 + node];
             }
             float q[NF];
 #pragma unroll
@@ -370,18 +373,17 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
                 const int ai = t / (TY * N2), r = t - ai * (TY * N2);
                 const int row = r / N2, pt = r - row * N2;
                 if (ai > txv || row >= tyv) continue;
-                const long long er = (long long)g.nx * (ey0 + row) + plane * z;
-                plane_interface<N, TX, TY, 0>(Qin, sT, sH, g, lm, lp, gamma, gm1, ai, row, txv,
+                const Ix er = (Ix)g.nx * (ey0 + row) + plane * z;
+                plane_interface<N, TX, TY, 0, Ix>(Qin, sT, sH, g, lm, lp, gamma, gm1, ai, row, txv,
                                               exL + er, exR + er, pt);
             } else if (t < CT::XT + CT::YT) {
                 const int u = t - CT::XT;
                 const int ai = u / (TX * N2), r = u - ai * (TX * N2);
                 const int cx = r / N2, pt = r - cx * N2;
                 if (ai > tyv || cx >= txv) continue;
-                const long long ec = ex0 + cx + plane * z;
-                plane_interface<N, TX, TY, 1>(Qin, sT, sH, g, lm, lp, gamma, gm1, ai, cx, tyv,
-                                              ec + (long long)g.nx * eyL,
-                                              ec + (long long)g.nx * eyR, pt);
+                const Ix ec = ex0 + cx + plane * z;
+                plane_interface<N, TX, TY, 1, Ix>(Qin, sT, sH, g, lm, lp, gamma, gm1, ai, cx, tyv,
+                                                  ec + (Ix)g.nx * eyL, ec + (Ix)g.nx * eyR, pt);
             } else {
                 const int u = t - CT::XT - CT::YT;
                 const int e2 = u / N2, pt = u - e2 * N2;
@@ -433,7 +435,7 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
                 acc += lmx * hx.x - lpx * hx.y;
                 acc += lmy * hy.x - lpy * hy.y;
                 acc += lmz * zm[n * N2 + pz] - lpz * zp[n * N2 + pz];
-                const long long o = sidx(n, e, node, g.E, N3);
+                const Ix o = ((Ix)n * E + e) * N3 + node;
                 if (MODE == 0) {
                     Out[o] = acc;
                 } else {
@@ -447,7 +449,7 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
         cp_async_wait_all();
         __syncthreads();
         if (z + 3 <= z1)
-            column_prefetch<N, TX, TY>(Qin, slots + ((z - z0 + 1) % 3) * CT::QSLOT, g, ex0, ey0,
+            column_prefetch<N, TX, TY, Ix>(Qin, slots + ((z - z0 + 1) % 3) * CT::QSLOT, g, ex0, ey0,
                                        txv, tyv, zmod(z + 3));
     }
 }

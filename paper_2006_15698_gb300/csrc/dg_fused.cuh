@@ -79,8 +79,9 @@ __device__ __forceinline__ void load_line(const float *p, float v[N])
 // Trace of an element on a face in direction DIR at node line (t1, t2):
 // sum_c l[c] Q(node c along DIR), from `src` (the element's field planes at
 // plane stride `pstride`); the same arithmetic for shared and global sources.
-template <int N, int DIR>
-__device__ __forceinline__ void line_trace(const float *src, long long pstride, int base,
+// Ix: index type of the state arrays (32-bit when every offset fits).
+template <int N, int DIR, typename Ix>
+__device__ __forceinline__ void line_trace(const float *src, Ix pstride, int base,
                                            const float *l, float q[NF])
 {
     constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? N : N * N);
@@ -150,23 +151,23 @@ struct FusedTile {
 
 // Neighbour table entry: >= 0 a global element index, < 0 the in-tile index
 // -(local + 1) of a neighbour that sits in the same tile.
-template <int N, int DIR, int TX, int TY>
+template <int N, int DIR, int TX, int TY, typename Ix>
 __device__ __forceinline__ void fused_face(const float *__restrict__ Qin, const float *sQ,
                                            float *sH, const long long *sNb, const Ops<float> &T,
-                                           long long E, int el, int side, int pt)
+                                           Ix E, int el, int side, int pt)
 {
     using FT = FusedTile<N, TX, TY>;
     constexpr int N2 = N * N, N3 = N * N * N;
     const int t1 = pt % N, t2 = pt / N;
     const int base = DIR == 0 ? (t2 * N + t1) * N : (DIR == 1 ? t2 * N2 + t1 : t2 * N + t1);
-    const long long nb = sNb[el * 6 + 2 * DIR + side];
+    const Ix nb = (Ix)sNb[el * 6 + 2 * DIR + side];
     // own trace at the face's end of the element, the neighbour's at the other end
     float qo[NF], qn[NF];
-    line_trace<N, DIR>(sQ + (size_t)el * FT::QSTR, N3, base, side ? T.lp : T.lm, qo);
+    line_trace<N, DIR, Ix>(sQ + (size_t)el * FT::QSTR, (Ix)N3, base, side ? T.lp : T.lm, qo);
     if (nb < 0)
-        line_trace<N, DIR>(sQ + (size_t)(-nb - 1) * FT::QSTR, N3, base, side ? T.lm : T.lp, qn);
+        line_trace<N, DIR, Ix>(sQ + (size_t)(-nb - 1) * FT::QSTR, (Ix)N3, base, side ? T.lm : T.lp, qn);
     else
-        line_trace<N, DIR>(Qin + nb * N3, E * N3, base, side ? T.lm : T.lp, qn);
+        line_trace<N, DIR, Ix>(Qin + nb * N3, E * N3, base, side ? T.lm : T.lp, qn);
     // left and right states by value selects (a pointer select between two
     // local arrays would force them out of registers)
     float qL[NF], qR[NF];
@@ -189,7 +190,8 @@ __device__ __forceinline__ void fused_face(const float *__restrict__ Qin, const 
 // extra threads only help with the face tasks).  MODE 0 writes the rhs to
 // Out, MODE 1 the LSERK stage update (dQ <- A dQ + dt R, Out <- Qin + B dQ).
 // Ends with a barrier, so a persistent caller may reuse `smem` at once.
-template <int N, int TX, int TY, int MODE>
+// Ix: index type of the state arrays (32-bit when every offset fits).
+template <int N, int TX, int TY, int MODE, typename Ix = long long>
 __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float *__restrict__ Out,
                                            float *__restrict__ dQ, const Ops<float> &T,
                                            const Geo &g, long long tile, float A, float B,
@@ -217,7 +219,8 @@ __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float 
     const int a = el % TX, b = el / TX;
     const bool in_tile = el < EPB;
     const bool active = in_tile && ex0 + a < g.nx && ey0 + b < g.ny;
-    const long long e = (long long)(ex0 + a) + (long long)g.nx * ((ey0 + b) + (long long)g.ny * bz);
+    const Ix E = (Ix)g.E;
+    const Ix e = (Ix)(ex0 + a) + (Ix)g.nx * ((ey0 + b) + (Ix)g.ny * bz);
     const int i = node % N, j = (node / N) % N, k = node / N2;
 
     for (int t = tid; t < EPB * 6; t += nthr) {  // the six neighbours of every element of the tile
@@ -234,7 +237,7 @@ __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float 
             if (cz == bz && la >= 0 && la < TX && lb >= 0 && lb < TY)
                 nb = -(long long)(lb * TX + la) - 1;
             else
-                nb = (long long)cx + (long long)g.nx * (cy + (long long)g.ny * cz);
+                nb = (long long)((Ix)cx + (Ix)g.nx * (cy + (Ix)g.ny * cz));
         }
         sNb[t] = nb;
     }
@@ -251,7 +254,7 @@ __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float 
     if (active) {
 #pragma unroll
         for (int n = 0; n < NF; ++n) {
-            q[n] = Qin[sidx(n, e, node, g.E, N3)];
+            q[n] = Qin[((Ix)n * E + e) * N3 + node];
             sQ[el * QSTR + n * N3 + node] = q[n];
         }
         const float rinv = fast_rcp(q[0]);
@@ -290,9 +293,9 @@ __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float 
         const int pt = r - el2 * N2;
         if (ex0 + el2 % TX >= g.nx || ey0 + el2 / TX >= g.ny) continue;
         const int side = face & 1;
-        if (face < 2) fused_face<N, 0, TX, TY>(Qin, sQ, sH, sNb, T, g.E, el2, side, pt);
-        else if (face < 4) fused_face<N, 1, TX, TY>(Qin, sQ, sH, sNb, T, g.E, el2, side, pt);
-        else fused_face<N, 2, TX, TY>(Qin, sQ, sH, sNb, T, g.E, el2, side, pt);
+        if (face < 2) fused_face<N, 0, TX, TY, Ix>(Qin, sQ, sH, sNb, T, E, el2, side, pt);
+        else if (face < 4) fused_face<N, 1, TX, TY, Ix>(Qin, sQ, sH, sNb, T, E, el2, side, pt);
+        else fused_face<N, 2, TX, TY, Ix>(Qin, sQ, sH, sNb, T, E, el2, side, pt);
     }
     __syncthreads();
 
@@ -328,7 +331,7 @@ __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float 
             acc += lmy * hy.x - lpy * hy.y;
             acc += lmz * hz.x - lpz * hz.y;
 
-            const long long o = sidx(n, e, node, g.E, N3);
+            const Ix o = ((Ix)n * E + e) * N3 + node;
             if (MODE == 0) {
                 Out[o] = acc;
             } else {
@@ -344,7 +347,7 @@ __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float 
 // one mesh: one tile per CTA
 // (at least 1280 resident threads per SM: the tile's phases are separated by
 // barriers, and other CTAs' warps fill the gaps)
-template <int N, int V, int MODE>
+template <int N, int V, int MODE, typename Ix>
 __global__ void __launch_bounds__(FusedTile<N, TileShape<N, V>::TX, TileShape<N, V>::TY>::THREADS,
                                   1280 / FusedTile<N, TileShape<N, V>::TX, TileShape<N, V>::TY>::THREADS)
     fused_stage_kernel(const float *__restrict__ Qin, float *__restrict__ Out,
@@ -353,8 +356,9 @@ __global__ void __launch_bounds__(FusedTile<N, TileShape<N, V>::TX, TileShape<N,
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const float dtr = MODE == 1 ? (float)(*dt) : 0.0f;
-    fused_tile<N, TileShape<N, V>::TX, TileShape<N, V>::TY, MODE>(Qin, Out, dQ, T, g, blockIdx.x,
-                                                                   A, B, dtr, smem_raw);
+    fused_tile<N, TileShape<N, V>::TX, TileShape<N, V>::TY, MODE, Ix>(Qin, Out, dQ, T, g,
+                                                                       blockIdx.x, A, B, dtr,
+                                                                       smem_raw);
 }
 
 // ---------------------------------------------------------------------------

@@ -711,16 +711,16 @@ cudaError_t launch_volume(const Geo &g, const Ops<real> &T, const real *Qin, rea
     return cudaGetLastError();
 }
 
-template <int N, int V, int MODE>
-cudaError_t launch_fused_v(const Geo &g, const Ops<float> &T, const float *Qin, float *Out,
-                           float *dQ, float A, float B, const double *dt, Prof *prof,
-                           cudaStream_t s)
+template <int N, int V, int MODE, typename Ix>
+cudaError_t launch_fused_ix(const Geo &g, const Ops<float> &T, const float *Qin, float *Out,
+                            float *dQ, float A, float B, const double *dt, Prof *prof,
+                            cudaStream_t s)
 {
     using SH = TileShape<N, V>;
     using FT = FusedTile<N, SH::TX, SH::TY>;
     const size_t smem = FT::BYTES;
     if (smem > 48 * 1024) {
-        cudaError_t err = cudaFuncSetAttribute(fused_stage_kernel<N, V, MODE>,
+        cudaError_t err = cudaFuncSetAttribute(fused_stage_kernel<N, V, MODE, Ix>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);
         if (err != cudaSuccess) return err;
@@ -728,9 +728,21 @@ cudaError_t launch_fused_v(const Geo &g, const Ops<float> &T, const float *Qin, 
     const long long blocks = tile_count(g, SH::TX, SH::TY);
     if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
     ProfScope ps(prof, kKindStage, s);
-    fused_stage_kernel<N, V, MODE><<<(unsigned)blocks, FT::THREADS, smem, s>>>(Qin, Out, dQ, T, g,
-                                                                                A, B, dt);
+    fused_stage_kernel<N, V, MODE, Ix><<<(unsigned)blocks, FT::THREADS, smem, s>>>(Qin, Out, dQ, T,
+                                                                                    g, A, B, dt);
     return cudaGetLastError();
+}
+
+// 32-bit index arithmetic when every offset into the state arrays fits
+template <int N, int V, int MODE>
+cudaError_t launch_fused_v(const Geo &g, const Ops<float> &T, const float *Qin, float *Out,
+                           float *dQ, float A, float B, const double *dt, Prof *prof,
+                           cudaStream_t s)
+{
+    const long long floats = (long long)NF * g.E * N * N * N;
+    if (floats <= 0x7fffffffLL)
+        return launch_fused_ix<N, V, MODE, int>(g, T, Qin, Out, dQ, A, B, dt, prof, s);
+    return launch_fused_ix<N, V, MODE, long long>(g, T, Qin, Out, dQ, A, B, dt, prof, s);
 }
 
 // the tile variant of order N selected for the single-mesh path (tuning table)
@@ -750,16 +762,16 @@ cudaError_t launch_fused(const Geo &g, const Ops<float> &T, const float *Qin, fl
 // Column kernel launch: the z range of every column is cut into chunks so
 // that the number of CTAs fills the GPU's resident slots in whole waves
 // (time ~ waves x (layers per chunk + the chunk's extra prologue layer)).
-template <int N, int MODE>
-cudaError_t launch_column(const Geo &g, const Ops<float> &T, const float *Qin, float *Out,
-                          float *dQ, float A, float B, const double *dt, Prof *prof,
-                          cudaStream_t s)
+template <int N, int MODE, typename Ix>
+cudaError_t launch_column_ix(const Geo &g, const Ops<float> &T, const float *Qin, float *Out,
+                             float *dQ, float A, float B, const double *dt, Prof *prof,
+                             cudaStream_t s)
 {
     using SH = ColShape<N, 0>;
     using CT = ColTile<N, SH::TX, SH::TY>;
     static int resident = 0;  // CTAs of this kernel resident on the device at once
     if (CT::BYTES > 48 * 1024) {
-        cudaError_t err = cudaFuncSetAttribute(column_stage_kernel<N, 0, MODE>,
+        cudaError_t err = cudaFuncSetAttribute(column_stage_kernel<N, 0, MODE, Ix>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)CT::BYTES);
         if (err != cudaSuccess) return err;
@@ -770,7 +782,7 @@ cudaError_t launch_column(const Geo &g, const Ops<float> &T, const float *Qin, f
         if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (err == cudaSuccess)
             err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, column_stage_kernel<N, 0, MODE>, CT::THREADS, CT::BYTES);
+                &per_sm, column_stage_kernel<N, 0, MODE, Ix>, CT::THREADS, CT::BYTES);
         if (err != cudaSuccess) return err;
         resident = sms * (per_sm > 0 ? per_sm : 1);
     }
@@ -787,9 +799,21 @@ cudaError_t launch_column(const Geo &g, const Ops<float> &T, const float *Qin, f
     const long long blocks = ncols * ((g.nz + best_zc - 1) / best_zc);
     if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
     ProfScope ps(prof, kKindStage, s);
-    column_stage_kernel<N, 0, MODE><<<(unsigned)blocks, CT::THREADS, CT::BYTES, s>>>(
+    column_stage_kernel<N, 0, MODE, Ix><<<(unsigned)blocks, CT::THREADS, CT::BYTES, s>>>(
         Qin, Out, dQ, T, g, A, B, dt, best_zc);
     return cudaGetLastError();
+}
+
+// 32-bit index arithmetic when every offset into the state arrays fits
+template <int N, int MODE>
+cudaError_t launch_column(const Geo &g, const Ops<float> &T, const float *Qin, float *Out,
+                          float *dQ, float A, float B, const double *dt, Prof *prof,
+                          cudaStream_t s)
+{
+    const long long floats = (long long)NF * g.E * N * N * N;
+    if (floats <= 0x7fffffffLL)
+        return launch_column_ix<N, MODE, int>(g, T, Qin, Out, dQ, A, B, dt, prof, s);
+    return launch_column_ix<N, MODE, long long>(g, T, Qin, Out, dQ, A, B, dt, prof, s);
 }
 
 // The float form runs the single-pass column stage (DRAM bound: one read of
