@@ -162,6 +162,24 @@ dg_status dg_rk_step(const dg_mesh *mesh, void *Q, void *dQ, const double *dt_de
 dg_status dg_norms(const dg_mesh *mesh, const void *Q, const void *Qref, double *out,
                    void *stream);
 
+/* nsteps steps of the loop "time step, LSERK45 step, integrals" in one call
+ * (an addition of this library, not in the paper).  For k = 0 .. nsteps-1:
+ *     dts[k]                     = the dg_cfl_dt time step of the current Q,
+ *     Q                          <- dg_rk_step(Q, dQ, &dts[k]),
+ *     integ[k*DG_NORMS_LEN ...]  = dg_norms(Q, NULL) of the new Q (if integ).
+ * The results are those of the separate calls, bit for bit.  The integrals
+ * of a step and the maximum wave speed for the next step's time step come
+ * from one pass over the new state; for DG_FP32 that pass also applies the
+ * fifth stage's update Q <- Q + B_5 dQ in place (the fifth stage writes only
+ * dQ), so the copy of the ping-pong state that dg_rk_step makes is not needed.
+ * dts and integ (nullable) are DEVICE arrays of nsteps and
+ * nsteps * DG_NORMS_LEN doubles; Q and dQ as for dg_rk_step.  A non-positive
+ * density or pressure met by any time-step evaluation sets the
+ * DG_ERR_NONFINITE flag as dg_cfl_dt does.  Errors: DG_ERR_ARG (NULL, Q == dQ,
+ * unaligned states, cfl <= 0, nsteps < 1). */
+dg_status dg_advance(const dg_mesh *mesh, void *Q, void *dQ, double cfl, int nsteps,
+                     double *dts, double *integ, void *stream);
+
 /* Per-kernel timing, the library's counterpart of the per-kernel breakdown
  * the paper reports (Sec. VI.B, Table II: Volume, Surface, Update-Project).
  * Between dg_profile_begin and dg_profile_end every kernel launch made for
@@ -179,11 +197,14 @@ dg_status dg_norms(const dg_mesh *mesh, const void *Q, const void *Qref, double 
  *                    or rhs write in one kernel (DG_FP32)
  *   DG_KERNEL_COPY   device copy of the second state back to Q after the
  *                    five ping-pong stages of a DG_FP32 step
+ *   DG_KERNEL_EPILOGUE dg_advance's pass at the end of a step: integrals and
+ *                    next time step (and the DG_FP32 fifth-stage update),
+ *                    with their one-block final reductions
  * ms and launches are HOST arrays of DG_PROFILE_KINDS entries.  Recording
  * costs one event pair per launch; begin discards earlier records. */
-#define DG_PROFILE_KINDS 7
+#define DG_PROFILE_KINDS 8
 enum { DG_KERNEL_FACE = 0, DG_KERNEL_VOLUME = 1, DG_KERNEL_CFL = 2, DG_KERNEL_NORMS = 3,
-       DG_KERNEL_INIT = 4, DG_KERNEL_STAGE = 5, DG_KERNEL_COPY = 6 };
+       DG_KERNEL_INIT = 4, DG_KERNEL_STAGE = 5, DG_KERNEL_COPY = 6, DG_KERNEL_EPILOGUE = 7 };
 dg_status dg_profile_begin(dg_mesh *mesh);
 dg_status dg_profile_end(dg_mesh *mesh, double *ms, int64_t *launches);
 

@@ -316,6 +316,21 @@ dg_status dg_rk_step(const dg_mesh *m, void *Q, void *dQ, const double *dt_dev, 
     return cuda_status(e);
 }
 
+dg_status dg_advance(const dg_mesh *m, void *Q, void *dQ, double cfl, int nsteps, double *dts,
+                     double *integ, void *stream)
+{
+    if (!m || !Q || !dQ || !dts || Q == dQ || !aligned16(Q) || !aligned16(dQ) || nsteps < 1 ||
+        !(cfl > 0.0) || !std::isfinite(cfl))
+        return DG_ERR_ARG;
+    dg::Work w = m->work;
+    cudaError_t e = m->prec == DG_FP64
+                        ? dg::Launch<double>::advance(m->geo, m->ops64, (double *)Q, (double *)dQ,
+                                                      cfl, nsteps, dts, integ, w, as_stream(stream))
+                        : dg::Launch<float>::advance(m->geo, m->ops32, (float *)Q, (float *)dQ,
+                                                     cfl, nsteps, dts, integ, w, as_stream(stream));
+    return cuda_status(e);
+}
+
 dg_status dg_norms(const dg_mesh *m, const void *Q, const void *Qref, double *out, void *stream)
 {
     if (!m || !Q || !out) return DG_ERR_ARG;

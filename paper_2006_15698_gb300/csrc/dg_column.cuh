@@ -224,7 +224,8 @@ __device__ __forceinline__ void plane_interface(const float *__restrict__ Qin, c
 }
 
 // One column chunk of the stage.  MODE 0 writes the rhs to Out, MODE 1 the
-// LSERK stage update (dQ <- A dQ + dt R, Out <- Qin + B dQ).  Ix is the index
+// LSERK stage update (dQ <- A dQ + dt R, Out <- Qin + B dQ), MODE 2 only its
+// dQ part (a step's last stage when a later pass applies Out <- Qin + B dQ).  Ix is the index
 // type of the state arrays: int when 5 E N^3 fits (32-bit address arithmetic
 // is measurably cheaper here), else a 64-bit integer.
 // (shared memory holds about four CTAs per SM; registers are sized for that)
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
     const int txv = min(TX, g.nx - ex0), tyv = min(TY, g.ny - ey0);
     const int z0 = chunk * zchunk;
     const int z1 = min(g.nz, z0 + zchunk);
-    const float dtr = MODE == 1 ? (float)(*dt) : 0.0f;
+    const float dtr = MODE != 0 ? (float)(*dt) : 0.0f;
     const float gamma = T.gamma, gm1 = T.gm1;
 
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
         // B: node fluxes, line traces; the node's dQ fetched early
         float dq[NF];
         if (active) {
-            if (MODE == 1 && A != 0.0f) {
+            if (MODE != 0 && A != 0.0f) {
 #pragma unroll
                 for (int n = 0; n < NF; ++n) dq[n] = dQ[((Ix)n * E + e) * N3 + node];
             }
@@ -425,23 +426,25 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
                 load_line<N>(f + 2 * NF * N3 + n * N3 + (j * N + i) * N, vz);
                 float acc = 0.0f;
 #pragma unroll
-                for (int c = 0; c < N; ++c) acc += dx[c] * vx[c];
+                for (int c = 0; c < N; ++c) acc = __fmaf_rn(dx[c], vx[c], acc);
 #pragma unroll
-                for (int c = 0; c < N; ++c) acc += dy[c] * vy[c];
+                for (int c = 0; c < N; ++c) acc = __fmaf_rn(dy[c], vy[c], acc);
 #pragma unroll
-                for (int c = 0; c < N; ++c) acc += dz[c] * vz[c];
+                for (int c = 0; c < N; ++c) acc = __fmaf_rn(dz[c], vz[c], acc);
                 const float2 hx = *reinterpret_cast<const float2 *>(h + ((0 * NF + n) * N2 + px) * 2);
                 const float2 hy = *reinterpret_cast<const float2 *>(h + ((1 * NF + n) * N2 + py) * 2);
-                acc += lmx * hx.x - lpx * hx.y;
-                acc += lmy * hy.x - lpy * hy.y;
-                acc += lmz * zm[n * N2 + pz] - lpz * zp[n * N2 + pz];
+                // explicitly rounded: every instantiation (rhs, stage, dQ-only
+                // last stage) gives the same floats
+                acc = __fmaf_rn(-lpx, hx.y, __fmaf_rn(lmx, hx.x, acc));
+                acc = __fmaf_rn(-lpy, hy.y, __fmaf_rn(lmy, hy.x, acc));
+                acc = __fmaf_rn(-lpz, zp[n * N2 + pz], __fmaf_rn(lmz, zm[n * N2 + pz], acc));
                 const Ix o = ((Ix)n * E + e) * N3 + node;
                 if (MODE == 0) {
                     Out[o] = acc;
                 } else {
-                    const float d = (A == 0.0f ? 0.0f : A * dq[n]) + dtr * acc;
+                    const float d = __fmaf_rn(dtr, acc, A == 0.0f ? 0.0f : __fmul_rn(A, dq[n]));
                     dQ[o] = d;
-                    Out[o] = cur[(n * EPB + el) * N3 + node] + B * d;
+                    if (MODE == 1) Out[o] = __fmaf_rn(B, d, cur[(n * EPB + el) * N3 + node]);
                 }
             }
         }

@@ -36,6 +36,24 @@ __device__ __forceinline__ float fast_sqrt(float x)
     return r;
 }
 
+// Wave-speed sum sum_d (|u_d| + c) of a float node, in float (the precision
+// of the state itself); false for rho <= 0, p <= 0 or NaN.  Every operation
+// explicitly rounded in a fixed order (no contraction), so every kernel that
+// evaluates it gets the same float; callers keep the maximum in float
+// (conversion to double is exact and monotonic) and the time step in double.
+__device__ __forceinline__ bool node_speed_f(float r, float mx, float my, float mz, float E,
+                                             float g, float &s)
+{
+    const float rinv = __fdiv_rn(1.0f, r);
+    const float u = __fmul_rn(mx, rinv), v = __fmul_rn(my, rinv), w = __fmul_rn(mz, rinv);
+    const float uu = __fadd_rn(__fadd_rn(__fmul_rn(u, u), __fmul_rn(v, v)), __fmul_rn(w, w));
+    const float p = __fmul_rn(g - 1.0f, __fsub_rn(E, __fmul_rn(__fmul_rn(0.5f, r), uu)));
+    if (!(r > 0.0f) || !(p > 0.0f)) return false;
+    const float c = __fsqrt_rn(__fmul_rn(__fmul_rn(g, p), rinv));
+    s = __fadd_rn(__fadd_rn(__fadd_rn(fabsf(u), c), __fadd_rn(fabsf(v), c)), __fadd_rn(fabsf(w), c));
+    return true;
+}
+
 template <int DIR>
 __device__ __forceinline__ void normal_flux_f(const float q[NF], float gamma, float gm1,
                                               float f[NF], float &speed)
@@ -188,7 +206,8 @@ __device__ __forceinline__ void fused_face(const float *__restrict__ Qin, const 
 
 // One tile of the stage with blockDim.x >= TX*TY*N^3 threads (one per node;
 // extra threads only help with the face tasks).  MODE 0 writes the rhs to
-// Out, MODE 1 the LSERK stage update (dQ <- A dQ + dt R, Out <- Qin + B dQ).
+// Out, MODE 1 the LSERK stage update (dQ <- A dQ + dt R, Out <- Qin + B dQ),
+// MODE 2 only its dQ part (a later pass applies Out <- Qin + B dQ).
 // Ends with a barrier, so a persistent caller may reuse `smem` at once.
 // Ix: index type of the state arrays (32-bit when every offset fits).
 template <int N, int TX, int TY, int MODE, typename Ix = long long>
@@ -318,26 +337,28 @@ __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float 
             load_line<N>(f + 2 * NF * N3 + n * N3 + (j * N + i) * N, vz);
             float acc = 0.0f;
 #pragma unroll
-            for (int c = 0; c < N; ++c) acc += dx[c] * vx[c];
+            for (int c = 0; c < N; ++c) acc = __fmaf_rn(dx[c], vx[c], acc);
 #pragma unroll
-            for (int c = 0; c < N; ++c) acc += dy[c] * vy[c];
+            for (int c = 0; c < N; ++c) acc = __fmaf_rn(dy[c], vy[c], acc);
 #pragma unroll
-            for (int c = 0; c < N; ++c) acc += dz[c] * vz[c];
+            for (int c = 0; c < N; ++c) acc = __fmaf_rn(dz[c], vz[c], acc);
             // lift: one (-, +) pair of face fluxes per direction
             const float2 hx = *reinterpret_cast<const float2 *>(h + ((0 * NF + n) * N2 + px) * 2);
             const float2 hy = *reinterpret_cast<const float2 *>(h + ((1 * NF + n) * N2 + py) * 2);
             const float2 hz = *reinterpret_cast<const float2 *>(h + ((2 * NF + n) * N2 + pz) * 2);
-            acc += lmx * hx.x - lpx * hx.y;
-            acc += lmy * hy.x - lpy * hy.y;
-            acc += lmz * hz.x - lpz * hz.y;
+            // explicitly rounded: every instantiation (rhs, stage, dQ-only
+            // last stage) gives the same floats
+            acc = __fmaf_rn(-lpx, hx.y, __fmaf_rn(lmx, hx.x, acc));
+            acc = __fmaf_rn(-lpy, hy.y, __fmaf_rn(lmy, hy.x, acc));
+            acc = __fmaf_rn(-lpz, hz.y, __fmaf_rn(lmz, hz.x, acc));
 
             const Ix o = ((Ix)n * E + e) * N3 + node;
             if (MODE == 0) {
                 Out[o] = acc;
             } else {
-                const float d = (A == 0.0f ? 0.0f : A * dQ[o]) + dtr * acc;
+                const float d = __fmaf_rn(dtr, acc, A == 0.0f ? 0.0f : __fmul_rn(A, dQ[o]));
                 dQ[o] = d;
-                Out[o] = q[n] + B * d;
+                if (MODE == 1) Out[o] = __fmaf_rn(B, d, q[n]);
             }
         }
     }
@@ -355,7 +376,7 @@ __global__ void __launch_bounds__(FusedTile<N, TileShape<N, V>::TX, TileShape<N,
                        const double *__restrict__ dt)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const float dtr = MODE == 1 ? (float)(*dt) : 0.0f;
+    const float dtr = MODE != 0 ? (float)(*dt) : 0.0f;
     fused_tile<N, TileShape<N, V>::TX, TileShape<N, V>::TY, MODE, Ix>(Qin, Out, dQ, T, g,
                                                                        blockIdx.x, A, B, dtr,
                                                                        smem_raw);
@@ -403,7 +424,7 @@ __global__ void __launch_bounds__(CLASS == 0 ? 256 : 352, CLASS == 0 ? 4 : 2)
         const InstDev &d = inst[item.inst];
         const float *src = parity == 0 ? d.Q : d.Qt;
         float *dst = parity == 0 ? d.Qt : d.Q;
-        const float dtr = MODE == 1 ? (float)(*d.dt) : 0.0f;
+        const float dtr = MODE != 0 ? (float)(*d.dt) : 0.0f;
 #define DG_CASE(NN, VV)                                                                       \
     case NN * 8 + VV:                                                                         \
         batched_tile<NN, VV, MODE>(src, dst, d.dQ, d.T, d.g, item.tile, A, B, dtr, smem_raw); \
@@ -433,26 +454,21 @@ __device__ __forceinline__ double tile_speed_max(const float *__restrict__ Q, co
     const int bx = (int)(tile % ntx), by = (int)((tile / ntx) % nty);
     const int bz = (int)(tile / ((long long)ntx * nty));
     constexpr int N3 = N * N * N;
-    double m = 0.0;
+    float m = 0.0f;  // float maximum of float speeds; converted once (exact)
     for (int t = threadIdx.x; t < TX * TY * N3; t += blockDim.x) {
         const int el = t / N3, node = t - el * N3;
         const int ex = bx * TX + el % TX, ey = by * TY + el / TX;
         if (ex >= g.nx || ey >= g.ny) continue;
         const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * bz);
         const long long o = e * N3 + node, pl = g.E * N3;
-        const float r = Q[o], mx = Q[pl + o], my = Q[2 * pl + o], mz = Q[3 * pl + o],
-                    E = Q[4 * pl + o];
-        const float rinv = 1.0f / r;
-        const float u = mx * rinv, v = my * rinv, w = mz * rinv;
-        const float p = (gamma - 1.0f) * (E - 0.5f * r * (u * u + v * v + w * w));
-        if (!(r > 0.0f) || !(p > 0.0f)) {
+        float sp;
+        if (!node_speed_f(Q[o], Q[pl + o], Q[2 * pl + o], Q[3 * pl + o], Q[4 * pl + o], gamma, sp)) {
             bad = true;
             continue;
         }
-        const float c = sqrtf(gamma * p * rinv);
-        m = fmax(m, (double)((fabsf(u) + c) + (fabsf(v) + c) + (fabsf(w) + c)));
+        m = fmaxf(m, sp);
     }
-    return m;
+    return (double)m;
 }
 
 static __global__ void __launch_bounds__(512)

@@ -157,6 +157,9 @@ struct Launch {
                            cudaStream_t s);
     static cudaError_t norms(const Geo &g, const real *Q, const real *Qref, double *out, Work &w,
                              cudaStream_t s);
+    // nsteps x (cfl time step -> dts[k], LSERK45 step, integrals -> integ[k * DG_NORMS_LEN])
+    static cudaError_t advance(const Geo &g, const Ops<real> &ops, real *Q, real *dQ, double cfl,
+                               int nsteps, double *dts, double *integ, Work &w, cudaStream_t s);
 };
 
 }  // namespace dg

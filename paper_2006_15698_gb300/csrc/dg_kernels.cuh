@@ -329,20 +329,7 @@ __device__ __forceinline__ bool node_speed(double r, double mx, double my, doubl
     s = __dadd_rn(__dadd_rn(__dadd_rn(fabs(u), c), __dadd_rn(fabs(v), c)), __dadd_rn(fabs(w), c));
     return true;
 }
-// Float state: the node's speed in float (the precision of the state itself),
-// the maximum and the time step in double.
-__device__ __forceinline__ bool node_speed(float r, float mx, float my, float mz, float E,
-                                           double gamma, double &s)
-{
-    const float g = (float)gamma;
-    const float rinv = 1.0f / r;
-    const float u = mx * rinv, v = my * rinv, w = mz * rinv;
-    const float p = (g - 1.0f) * (E - 0.5f * r * (u * u + v * v + w * w));
-    if (!(r > 0.0f) || !(p > 0.0f)) return false;
-    const float c = sqrtf(g * p * rinv);
-    s = (double)((fabsf(u) + c) + (fabsf(v) + c) + (fabsf(w) + c));
-    return true;
-}
+// (float state: node_speed_f, with the float form's kernels)
 
 // Float estimate of a double node's wave-speed sum, used only to skip the
 // exact evaluation of nodes that cannot hold the maximum.  Returns true when
@@ -368,19 +355,67 @@ __device__ __forceinline__ bool node_speed_estimate(double r, double mx, double 
            fabsf(zf) <= big && fabsf(ef) <= big && p >= 0.01f * ef && s >= 1e-20f;
 }
 
-// Lambda = max over nodes of sum_d (|u_d| + c), reduced in double; a node with
-// rho <= 0, p <= 0 or NaN contributes a NaN whose bit pattern is above every
-// finite value, and raises the error flag.
+// One warp-synchronous step of the double-state Lambda reduction (all 32
+// lanes call it together; `in` marks the lanes that hold a node).
 //
-// Double state: the exact speed (IEEE divisions and square root) costs about
-// fifty FP64-pipe instructions, so each warp first estimates its 32 nodes'
-// speeds in float and keeps R, the running maximum of its well-conditioned
+// The exact speed (IEEE divisions and square root) costs about fifty
+// FP64-pipe instructions, so each warp first estimates its 32 nodes' speeds
+// in float and keeps R, the running maximum of its well-conditioned
 // estimates.  Only nodes whose estimate reaches R (1 - 8 kSpeedTol), and the
 // nodes without a trustworthy estimate, are evaluated exactly.  The node x
 // holding the exact maximum S is always among them: its estimate is at least
 // S (1 - tol) while R is at most S (1 + tol), and (1 - tol) >= (1 + tol)
 // (1 - 8 tol).  The result is therefore the same double as the full
 // evaluation, bit for bit.
+__device__ __forceinline__ void pruned_speed_step(bool in, double r, double mx, double my,
+                                                  double mz, double E, double gamma, float &R,
+                                                  double &m, bool &bad)
+{
+    const float keep = 1.0f - 8.0f * kSpeedTol;
+    float sf = 0.0f;
+    bool ok = false;
+    if (in) ok = node_speed_estimate(r, mx, my, mz, E, (float)gamma, sf);
+    float wm = ok ? sf : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+    R = fmaxf(R, wm);
+    if (in && (!ok || sf >= R * keep)) {
+        double s;
+        if (node_speed(r, mx, my, mz, E, gamma, s)) m = fmax(m, s);
+        else bad = true;
+    }
+}
+
+// NaN-propagating block maximum of non-negative doubles (compared as bit
+// patterns) merged into *lam_bits; a thread that saw a bad node raises *err
+// and contributes a NaN, whose bit pattern is above every finite value.
+// Called by every thread of the block (blockDim.x <= 256).
+__device__ __forceinline__ void block_lambda(double m, bool bad, unsigned long long *lam_bits,
+                                             int *err)
+{
+    __shared__ unsigned long long redb[8];
+    if (bad) {
+        atomicOr(err, 1);
+        m = __longlong_as_double(0x7ff8000000000000LL);
+    }
+    unsigned long long b = (unsigned long long)__double_as_longlong(m);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long x = __shfl_xor_sync(0xffffffffu, b, o);
+        b = x > b ? x : b;
+    }
+    if ((threadIdx.x & 31) == 0) redb[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long mb = redb[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mb = redb[w] > mb ? redb[w] : mb;
+        atomicMax(lam_bits, mb);
+    }
+}
+
+// Lambda = max over nodes of sum_d (|u_d| + c), reduced in double; a node with
+// rho <= 0, p <= 0 or NaN contributes a NaN and raises the error flag.
+// Double state: the float pre-filter above; float state: node speeds in float.
 template <typename real>
 __global__ void __launch_bounds__(256) cfl_kernel(const real *__restrict__ Q, long long nodes,
                                                   double gamma, unsigned long long *lam_bits,
@@ -389,8 +424,6 @@ __global__ void __launch_bounds__(256) cfl_kernel(const real *__restrict__ Q, lo
     double m = 0.0;
     bool bad = false;
     if constexpr (std::is_same<real, double>::value) {
-        const float gf = (float)gamma;
-        const float keep = 1.0f - 8.0f * kSpeedTol;
         const int lane = threadIdx.x & 31;
         const long long stride = (long long)gridDim.x * blockDim.x;  // a multiple of 32
         float R = 0.0f;
@@ -400,54 +433,28 @@ __global__ void __launch_bounds__(256) cfl_kernel(const real *__restrict__ Q, lo
             const long long t = tb + lane;
             const bool in = t < nodes;
             double r = 1.0, mx = 0.0, my = 0.0, mz = 0.0, E = 0.0;
-            float sf = 0.0f;
-            bool ok = false;
             if (in) {
                 r = Q[t]; mx = Q[nodes + t]; my = Q[2 * nodes + t]; mz = Q[3 * nodes + t];
                 E = Q[4 * nodes + t];
-                ok = node_speed_estimate(r, mx, my, mz, E, gf, sf);
             }
-            float wm = ok ? sf : 0.0f;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
-            R = fmaxf(R, wm);
-            if (in && (!ok || sf >= R * keep)) {
-                double s;
-                if (node_speed(r, mx, my, mz, E, gamma, s)) m = fmax(m, s);
-                else bad = true;
-            }
+            pruned_speed_step(in, r, mx, my, mz, E, gamma, R, m, bad);
         }
     } else {
+        const float gf = (float)gamma;
+        float mf = 0.0f;
         for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nodes;
              t += (long long)gridDim.x * blockDim.x) {
-            double s;
-            if (!node_speed(Q[t], Q[nodes + t], Q[2 * nodes + t], Q[3 * nodes + t],
-                            Q[4 * nodes + t], gamma, s)) {
+            float sp;
+            if (!node_speed_f(Q[t], Q[nodes + t], Q[2 * nodes + t], Q[3 * nodes + t],
+                              Q[4 * nodes + t], gf, sp)) {
                 bad = true;
                 continue;
             }
-            m = fmax(m, s);
+            mf = fmaxf(mf, sp);
         }
+        m = (double)mf;
     }
-    if (bad) {
-        atomicOr(err, 1);
-        m = __longlong_as_double(0x7ff8000000000000LL);
-    }
-    // NaN-propagating max over the block: compare bit patterns of non-negative doubles
-    unsigned long long b = (unsigned long long)__double_as_longlong(m);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long x = __shfl_xor_sync(0xffffffffu, b, o);
-        b = x > b ? x : b;
-    }
-    __shared__ unsigned long long redb[8];
-    if ((threadIdx.x & 31) == 0) redb[threadIdx.x >> 5] = b;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long mb = redb[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mb = redb[w] > mb ? redb[w] : mb;
-        atomicMax(lam_bits, mb);
-    }
+    block_lambda(m, bad, lam_bits, err);
 }
 
 static __global__ void cfl_finalize_kernel(unsigned long long *lam_bits, double cfl, double hmin,
@@ -484,22 +491,82 @@ __device__ __forceinline__ void ff_accumulate(float &hi, float &lo, float wh, fl
     lo += err + fmaf(wl, x, e);
 }
 
+// Shared per-block part of the integrals: the node weights (double, and split
+// into two floats for the float state).
+struct NormsShared {
+    double red[8][256];
+    double sw[NMAX * NMAX * NMAX];
+    float swh[NMAX * NMAX * NMAX], swl[NMAX * NMAX * NMAX];
+};
+
+__device__ __forceinline__ void norms_stage_weights(NormsShared &sh, const NodeWeights &W, int N3)
+{
+    for (int t = threadIdx.x; t < N3; t += blockDim.x) {
+        sh.sw[t] = W.w[t];
+        sh.swh[t] = (float)W.w[t];
+        sh.swl[t] = (float)(W.w[t] - (double)sh.swh[t]);
+    }
+    __syncthreads();
+}
+
+// One node's contribution to I_0..I_4 and KE (weight index nd).
+template <typename real>
+__device__ __forceinline__ void norms_node(const NormsShared &sh, int nd, const real qr[NF],
+                                           double acc[8], float fh[6], float fl[6])
+{
+    if constexpr (sizeof(real) == 4) {
+        const float wh = sh.swh[nd], wl = sh.swl[nd];
+#pragma unroll
+        for (int n = 0; n < NF; ++n) ff_accumulate(fh[n], fl[n], wh, wl, qr[n]);
+        // the kinetic-energy density in float (the state's own precision)
+        const float mm = __fadd_rn(__fadd_rn(__fmul_rn(qr[1], qr[1]), __fmul_rn(qr[2], qr[2])),
+                                   __fmul_rn(qr[3], qr[3]));
+        const float ke = __fmul_rn(__fmul_rn(0.5f, mm), fast_rcp(qr[0]));
+        ff_accumulate(fh[5], fl[5], wh, wl, ke);
+    } else {
+        const double wq = sh.sw[nd];
+#pragma unroll
+        for (int n = 0; n < NF; ++n) acc[n] += wq * qr[n];
+        acc[5] += wq * 0.5 * (qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]) * recip(qr[0]);
+    }
+}
+
+// The block's sums (thread sums, then a fixed shared-memory tree) -> partials.
+template <typename real>
+__device__ __forceinline__ void norms_block_store(NormsShared &sh, double acc[8], const float fh[6],
+                                                  const float fl[6], double *partials)
+{
+    if constexpr (sizeof(real) == 4) {
+#pragma unroll
+        for (int v = 0; v < 6; ++v) acc[v] = (double)fh[v] + (double)fl[v];
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) sh.red[v][threadIdx.x] = acc[v];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) sh.red[v][threadIdx.x] += sh.red[v][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) partials[blockIdx.x * 8 + threadIdx.x] = sh.red[threadIdx.x][0];
+}
+
+// Nodes per thread per loop trip of the integral sweeps: their loads are all
+// issued before any is used, for more DRAM requests in flight per thread.
+template <typename real>
+constexpr int kSweepU = sizeof(real) == 4 ? 4 : 2;
+
 template <typename real>
 __global__ void __launch_bounds__(256) norms_partial_kernel(const real *__restrict__ Q,
                                                             const real *__restrict__ Qref,
                                                             const Geo g, const NodeWeights W,
                                                             double *partials)
 {
-    __shared__ double red[8][256];
-    __shared__ double sw[NMAX * NMAX * NMAX];  // weights by node (thread-varying index)
-    __shared__ float swh[NMAX * NMAX * NMAX], swl[NMAX * NMAX * NMAX];
+    constexpr int U = kSweepU<real>;
+    __shared__ NormsShared sh;
     const int N = g.p + 1, N3 = N * N * N;
-    for (int t = threadIdx.x; t < N3; t += blockDim.x) {
-        sw[t] = W.w[t];
-        swh[t] = (float)W.w[t];
-        swl[t] = (float)(W.w[t] - (double)swh[t]);
-    }
-    __syncthreads();
+    norms_stage_weights(sh, W, N3);
     const long long nodes = g.E * N3;
     const long long chunk = (nodes + gridDim.x - 1) / gridDim.x;
     const long long beg = (long long)blockIdx.x * chunk;
@@ -509,50 +576,134 @@ __global__ void __launch_bounds__(256) norms_partial_kernel(const real *__restri
     // in-element node index of t, advanced by the stride without a division
     int node = (int)((beg + threadIdx.x) % N3);
     const int step = (int)(blockDim.x % N3);
-    for (long long t = beg + threadIdx.x; t < end; t += blockDim.x) {
-        const int nd = node;
-        node += step;
-        if (node >= N3) node -= N3;
-        real qr[NF];
+    const int bd = blockDim.x;
+    // the thread's nodes beg + threadIdx.x + k blockDim.x in order of k
+    for (long long t0 = beg + threadIdx.x; t0 < end; t0 += (long long)U * bd) {
+        real qr[U][NF];
+        int nd[U];
+        // loads of all U nodes first (indices past the end clamped to the
+        // block's last node, so the loads need no branch)
 #pragma unroll
-        for (int n = 0; n < NF; ++n) qr[n] = Q[n * nodes + t];
-        if constexpr (sizeof(real) == 4) {
-            const float wh = swh[nd], wl = swl[nd];
+        for (int u = 0; u < U; ++u) {
+            long long t = t0 + (long long)u * bd;
+            t = t < end ? t : end - 1;
+            nd[u] = node;
+            node += step;
+            if (node >= N3) node -= N3;
 #pragma unroll
-            for (int n = 0; n < NF; ++n) ff_accumulate(fh[n], fl[n], wh, wl, qr[n]);
-            // the kinetic-energy density in float (the state's own precision)
-            const float ke = 0.5f * (qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]) * fast_rcp(qr[0]);
-            ff_accumulate(fh[5], fl[5], wh, wl, ke);
-        } else {
-            const double wq = sw[nd];
-#pragma unroll
-            for (int n = 0; n < NF; ++n) acc[n] += wq * qr[n];
-            acc[5] += wq * 0.5 * (qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]) * recip(qr[0]);
+            for (int n = 0; n < NF; ++n) qr[u][n] = Q[n * nodes + t];
         }
-        if (Qref) {
-            const double wq = sw[nd];
 #pragma unroll
-            for (int n = 0; n < NF; ++n) {
-                const double q = (double)qr[n], r = (double)Qref[n * nodes + t];
-                acc[6] += wq * (q - r) * (q - r);
-                acc[7] += wq * r * r;
+        for (int u = 0; u < U; ++u) {
+            const long long t = t0 + (long long)u * bd;
+            if (t >= end) break;
+            norms_node<real>(sh, nd[u], qr[u], acc, fh, fl);
+            if (Qref) {
+                const double wq = sh.sw[nd[u]];
+#pragma unroll
+                for (int n = 0; n < NF; ++n) {
+                    const double q = (double)qr[u][n], r = (double)Qref[n * nodes + t];
+                    acc[6] += wq * (q - r) * (q - r);
+                    acc[7] += wq * r * r;
+                }
             }
         }
     }
-    if constexpr (sizeof(real) == 4) {
+    norms_block_store<real>(sh, acc, fh, fl, partials);
+}
+
+// Step epilogue of dg_advance, one pass over the state a step ends with:
+// UPDATE applies the float form's fifth-stage update Q <- Q + B dQ in place
+// (the fifth stage wrote only dQ); then the integrals of the new state (the
+// partition, order and arithmetic of norms_partial_kernel without Qref, so
+// the sums are those of dg_norms bit for bit) and, if CFL, its Lambda
+// maximum for the next step's time step (the node speeds of cfl_kernel).
+template <typename real, bool UPDATE, bool CFL, bool NORMS>
+__global__ void __launch_bounds__(256) step_epilogue_kernel(real *Q, const real *__restrict__ dQ,
+                                                            real B, const Geo g,
+                                                            const NodeWeights W, double *partials,
+                                                            unsigned long long *lam_bits, int *err)
+{
+    constexpr int U = kSweepU<real>;
+    __shared__ NormsShared sh;
+    const int N = g.p + 1, N3 = N * N * N;
+    norms_stage_weights(sh, W, N3);
+    const long long nodes = g.E * N3;
+    const long long chunk = (nodes + gridDim.x - 1) / gridDim.x;
+    const long long beg = (long long)blockIdx.x * chunk;
+    const long long end = beg + chunk < nodes ? beg + chunk : nodes;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    float fh[6] = {0, 0, 0, 0, 0, 0}, fl[6] = {0, 0, 0, 0, 0, 0};
+    double m = 0.0;
+    float mf = 0.0f;
+    bool bad = false;
+    float R = 0.0f;
+    const float gf = (float)g.gamma;
+    int node = (int)((beg + threadIdx.x) % N3);
+    const int step = (int)(blockDim.x % N3);
+    const int bd = blockDim.x;
+    const int lane = threadIdx.x & 31;
+    // whole warps walk together (the double-state pre-filter shuffles); each
+    // lane sees the nodes beg + threadIdx.x + k blockDim.x in order of k, as
+    // in the integrals
+    for (long long tb = beg + (threadIdx.x & ~31); tb < end; tb += (long long)U * bd) {
+        real qr[U][NF];
+        int nd[U];
+        bool in[U];
+        // loads of all U nodes first (indices past the end clamped to the
+        // block's last node, so the loads need no branch)
 #pragma unroll
-        for (int v = 0; v < 6; ++v) acc[v] = (double)fh[v] + (double)fl[v];
+        for (int u = 0; u < U; ++u) {
+            long long t = tb + (long long)u * bd + lane;
+            in[u] = t < end;
+            t = in[u] ? t : end - 1;
+            nd[u] = node;
+            node += step;
+            if (node >= N3) node -= N3;
+#pragma unroll
+            for (int n = 0; n < NF; ++n) qr[u][n] = Q[n * nodes + t];
+            if constexpr (UPDATE) {
+                real d[NF];
+#pragma unroll
+                for (int n = 0; n < NF; ++n) d[n] = dQ[n * nodes + t];
+#pragma unroll
+                for (int n = 0; n < NF; ++n) {
+                    if constexpr (sizeof(real) == 4) qr[u][n] = __fmaf_rn(B, d[n], qr[u][n]);
+                    else qr[u][n] = __fma_rn(B, d[n], qr[u][n]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long t = tb + (long long)u * bd + lane;
+            if constexpr (UPDATE) {
+                if (in[u]) {
+#pragma unroll
+                    for (int n = 0; n < NF; ++n) Q[n * nodes + t] = qr[u][n];
+                }
+            }
+            if constexpr (NORMS) {
+                if (in[u]) norms_node<real>(sh, nd[u], qr[u], acc, fh, fl);
+            }
+            if constexpr (CFL) {
+                if constexpr (std::is_same<real, double>::value) {
+                    pruned_speed_step(in[u], qr[u][0], qr[u][1], qr[u][2], qr[u][3], qr[u][4],
+                                      g.gamma, R, m, bad);
+                } else if (in[u]) {
+                    float sp;
+                    if (node_speed_f(qr[u][0], qr[u][1], qr[u][2], qr[u][3], qr[u][4], gf, sp))
+                        mf = fmaxf(mf, sp);
+                    else
+                        bad = true;
+                }
+            }
+        }
     }
-#pragma unroll
-    for (int v = 0; v < 8; ++v) red[v][threadIdx.x] = acc[v];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s)
-#pragma unroll
-            for (int v = 0; v < 8; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + s];
-        __syncthreads();
+    if constexpr (NORMS) norms_block_store<real>(sh, acc, fh, fl, partials);
+    if constexpr (CFL) {
+        if constexpr (sizeof(real) == 4) m = (double)mf;
+        block_lambda(m, bad, lam_bits, err);
     }
-    if (threadIdx.x < 8) partials[blockIdx.x * 8 + threadIdx.x] = red[threadIdx.x][0];
 }
 
 // Pass 2: one block sums the partials in a fixed order.
@@ -661,7 +812,7 @@ inline int grid_for(long long n, int threads, long long cap)
 
 // kernel kinds of the per-kernel timing (dg_profile_end)
 enum { kKindFace = 0, kKindVolume = 1, kKindCfl = 2, kKindNorms = 3, kKindInit = 4, kKindStage = 5,
-       kKindCopy = 6 };
+       kKindCopy = 6, kKindEpilogue = 7 };
 
 struct ProfScope {
     Prof *p;
@@ -836,25 +987,30 @@ cudaError_t rhs_n(const Geo &g, const Ops<real> &T, const real *Q, real *R, Work
     }
 }
 
+// One LSERK45 step.  Float form: ping-pong between Q and the handle's second
+// state; the fifth stage ends in the second state, copied back so the result
+// is in Q -- unless last_dq_only, where the fifth stage writes only dQ, Q
+// holds the fourth stage's state, and the caller applies Q <- Q + B_5 dQ.
 template <int N, typename real>
 cudaError_t rk_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, const double *dt, Work &w,
-                 cudaStream_t s)
+                 cudaStream_t s, bool last_dq_only = false)
 {
     if constexpr (std::is_same<real, float>::value) {
-        // ping-pong between Q and the handle's second state: five stages end
-        // in the second state, copied back so the result is in Q
         real *Tq = static_cast<real *>(w.qtmp);
         for (int st = 0; st < 5; ++st) {
             const real *src = (st % 2 == 0) ? Q : Tq;
             real *dst = (st % 2 == 0) ? Tq : Q;
-            cudaError_t err =
-                column_stage(N)
-                    ? launch_column<N, 1>(g, T, src, dst, dQ, float(kRkA[st]), float(kRkB[st]),
-                                          dt, w.prof, s)
-                    : launch_fused<N, 1>(g, T, src, dst, dQ, float(kRkA[st]), float(kRkB[st]),
-                                         dt, w.prof, s);
+            const float A = float(kRkA[st]), B = float(kRkB[st]);
+            cudaError_t err;
+            if (st == 4 && last_dq_only)
+                err = column_stage(N) ? launch_column<N, 2>(g, T, src, dst, dQ, A, B, dt, w.prof, s)
+                                      : launch_fused<N, 2>(g, T, src, dst, dQ, A, B, dt, w.prof, s);
+            else
+                err = column_stage(N) ? launch_column<N, 1>(g, T, src, dst, dQ, A, B, dt, w.prof, s)
+                                      : launch_fused<N, 1>(g, T, src, dst, dQ, A, B, dt, w.prof, s);
             if (err != cudaSuccess) return err;
         }
+        if (last_dq_only) return cudaSuccess;
         const size_t bytes = (size_t)NF * (size_t)g.E * N * N * N * sizeof(real);
         ProfScope ps(w.prof, kKindCopy, s);
         return cudaMemcpyAsync(Q, Tq, bytes, cudaMemcpyDeviceToDevice, s);
@@ -870,6 +1026,31 @@ cudaError_t rk_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, const doub
         return cudaSuccess;
     }
 }
+
+// host table of the quadrature weight of every in-element node
+inline NodeWeights node_weights(const Geo &g)
+{
+    NodeWeights W;
+    const int N = g.p + 1;
+    for (int k = 0; k < N; ++k)
+        for (int j = 0; j < N; ++j)
+            for (int i = 0; i < N; ++i) W.w[(k * N + j) * N + i] = g.J * (g.w[i] * g.w[j] * g.w[k]);
+    return W;
+}
+
+template <typename real, bool UPDATE, bool CFL, bool NORMS>
+void launch_epilogue(real *Q, const real *dQ, real B, const Geo &g, const NodeWeights &W, Work &w,
+                     cudaStream_t s)
+{
+    step_epilogue_kernel<real, UPDATE, CFL, NORMS><<<kNormBlocks, 256, 0, s>>>(
+        Q, dQ, B, g, W, w.partials, w.lam_bits, w.err);
+}
+
+// nsteps steps of (time step, LSERK45 step, integrals); the end of a step and
+// the start of the next share one pass over the state (step_epilogue_kernel).
+template <int N, typename real>
+cudaError_t advance_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, double cfl, int nsteps,
+                      double *dts, double *integ, Work &w, cudaStream_t s);
 
 #define DG_DISPATCH_P(p, CALL)            \
     switch (p) {                          \
@@ -920,11 +1101,7 @@ template <typename real>
 cudaError_t Launch<real>::norms(const Geo &g, const real *Q, const real *Qref, double *out,
                                 Work &w, cudaStream_t s)
 {
-    NodeWeights W;
-    const int N = g.p + 1;
-    for (int k = 0; k < N; ++k)
-        for (int j = 0; j < N; ++j)
-            for (int i = 0; i < N; ++i) W.w[(k * N + j) * N + i] = g.J * (g.w[i] * g.w[j] * g.w[k]);
+    const NodeWeights W = node_weights(g);
     ProfScope ps(w.prof, kKindNorms, s);
     norms_partial_kernel<real><<<kNormBlocks, 256, 0, s>>>(Q, Qref, g, W, w.partials);
     cudaError_t err = cudaGetLastError();
@@ -944,6 +1121,76 @@ cudaError_t Launch<real>::init(const Geo &g, int kind, const double *params, rea
     ProfScope ps(w.prof, kKindInit, s);
     init_kernel<real><<<grid_for(nodes, 256, 152 * 16), 256, 0, s>>>(g, kind, prm, Q);
     return cudaGetLastError();
+}
+
+template <int N, typename real>
+cudaError_t advance_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, double cfl, int nsteps,
+                      double *dts, double *integ, Work &w, cudaStream_t s)
+{
+    constexpr bool kFloat = std::is_same<real, float>::value;
+    const NodeWeights W = node_weights(g);
+    cudaError_t err = Launch<real>::cfl(g, Q, cfl, dts, w, s);
+    if (err != cudaSuccess) return err;
+    const real B5 = real(kRkB[4]);
+    for (int k = 0; k < nsteps; ++k) {
+        err = rk_n<N, real>(g, T, Q, dQ, dts + k, w, s, kFloat);
+        if (err != cudaSuccess) return err;
+        const bool more = k + 1 < nsteps, norms = integ != nullptr;
+        if constexpr (!kFloat) {
+            // double state: the integrals are FP64-pipe bound and the time
+            // step's pre-filter is warp-synchronous; one pass doing both was
+            // measured slower than the two passes, which it would only save
+            // one read of the state
+            if (norms) {
+                err = Launch<real>::norms(g, Q, nullptr, integ + (size_t)k * DG_NORMS_LEN, w, s);
+                if (err != cudaSuccess) return err;
+            }
+            if (more) {
+                err = Launch<real>::cfl(g, Q, cfl, dts + k + 1, w, s);
+                if (err != cudaSuccess) return err;
+            }
+            continue;
+        }
+        ProfScope ps(w.prof, kKindEpilogue, s);
+        if (more && norms) launch_epilogue<real, kFloat, true, true>(Q, dQ, B5, g, W, w, s);
+        else if (more) launch_epilogue<real, kFloat, true, false>(Q, dQ, B5, g, W, w, s);
+        else if (norms) launch_epilogue<real, kFloat, false, true>(Q, dQ, B5, g, W, w, s);
+        else if (kFloat) launch_epilogue<real, kFloat, false, false>(Q, dQ, B5, g, W, w, s);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        if (norms) {
+            norms_final_kernel<<<1, 256, 0, s>>>(w.partials, kNormBlocks, 0, integ + (size_t)k * DG_NORMS_LEN);
+            err = cudaGetLastError();
+            if (err != cudaSuccess) return err;
+        }
+        if (more) {
+            cfl_finalize_kernel<<<1, 1, 0, s>>>(w.lam_bits, cfl, g.hmin, g.p, dts + k + 1);
+            err = cudaGetLastError();
+            if (err != cudaSuccess) return err;
+        }
+    }
+    return cudaSuccess;
+}
+
+// Explicit instantiation of the per-degree launch paths of one scalar type:
+// DG_INSTANTIATE_N(template, NN, real) defines them (one translation unit per
+// group of degrees compiles them in parallel), DG_INSTANTIATE_N(extern
+// template, NN, real) declares them elsewhere.
+#define DG_INSTANTIATE_N(KW, NN, REAL)                                                        \
+    KW cudaError_t rhs_n<NN, REAL>(const Geo &, const Ops<REAL> &, const REAL *, REAL *, Work &, \
+                                   cudaStream_t);                                            \
+    KW cudaError_t rk_n<NN, REAL>(const Geo &, const Ops<REAL> &, REAL *, REAL *,             \
+                                  const double *, Work &, cudaStream_t, bool);               \
+    KW cudaError_t advance_n<NN, REAL>(const Geo &, const Ops<REAL> &, REAL *, REAL *, double, \
+                                       int, double *, double *, Work &, cudaStream_t);
+
+template <typename real>
+cudaError_t Launch<real>::advance(const Geo &g, const Ops<real> &T, real *Q, real *dQ, double cfl,
+                                  int nsteps, double *dts, double *integ, Work &w, cudaStream_t s)
+{
+#define DG_CALL(NN) advance_n<NN, real>(g, T, Q, dQ, cfl, nsteps, dts, integ, w, s)
+    DG_DISPATCH_P(g.p, DG_CALL)
+#undef DG_CALL
 }
 
 }  // namespace dg

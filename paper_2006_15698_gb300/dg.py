@@ -53,6 +53,8 @@ _lib.dg_rk_step.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.dg_rk_step.restype = ctypes.c_int
 _lib.dg_norms.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.dg_norms.restype = ctypes.c_int
+_lib.dg_advance.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _vp, _vp, _vp]
+_lib.dg_advance.restype = ctypes.c_int
 _lib.dg_status_string.argtypes = [ctypes.c_int]
 _lib.dg_status_string.restype = ctypes.c_char_p
 _lib.dg_last_error.argtypes = [_vp]
@@ -107,8 +109,8 @@ _lib.dg_batch_norms.restype = ctypes.c_int
 _lib.dg_batch_last_error.argtypes = [_vp]
 _lib.dg_batch_last_error.restype = ctypes.c_int
 
-DG_PROFILE_KINDS = 7
-KERNEL_KINDS = ("face", "volume", "cfl", "norms", "init", "stage", "copy")
+DG_PROFILE_KINDS = 8
+KERNEL_KINDS = ("face", "volume", "cfl", "norms", "init", "stage", "copy", "epilogue")
 DG_ERR_TOO_LARGE = 8
 DG_STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -175,6 +177,11 @@ def dg_rk_step(h, Q, dQ, dt_dev, stream=None):
 
 def dg_norms(h, Q, Qref, out_dev, stream=None):
     _check(_lib.dg_norms(h, _ptr(Q), _ptr(Qref), _ptr(out_dev), _stream(stream)), "dg_norms")
+
+
+def dg_advance(h, Q, dQ, cfl, nsteps, dts_dev, integ_dev, stream=None):
+    _check(_lib.dg_advance(h, _ptr(Q), _ptr(dQ), cfl, nsteps, _ptr(dts_dev), _ptr(integ_dev),
+                           _stream(stream)), "dg_advance")
 
 
 def dg_status_string(st):
@@ -266,6 +273,17 @@ class Mesh:
         out = torch.empty(DG_NORMS_LEN, dtype=torch.float64, device=self.device) if out is None else out
         dg_norms(self.h, self._chk(Q), None if Qref is None else self._chk(Qref), out, stream)
         return out
+
+    def advance(self, Q, dQ, cfl, nsteps, dts=None, integ=None, with_integrals=True, stream=None):
+        """nsteps x (time step, LSERK45 step, integrals of the new state) in
+        one call; returns (dts, integ): device arrays of nsteps and
+        (nsteps, DG_NORMS_LEN) doubles (integ None when not requested)."""
+        if dts is None:
+            dts = torch.empty(nsteps, dtype=torch.float64, device=self.device)
+        if integ is None and with_integrals:
+            integ = torch.empty((nsteps, DG_NORMS_LEN), dtype=torch.float64, device=self.device)
+        dg_advance(self.h, self._chk(Q), self._chk(dQ), cfl, nsteps, dts, integ, stream)
+        return dts, integ
 
     def last_error(self):
         return dg_last_error(self.h)
