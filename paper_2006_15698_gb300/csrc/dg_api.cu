@@ -502,6 +502,8 @@ struct dg_batch {
     double *d_partials = nullptr;
     std::vector<void *> qt;             // second states owned by the batch
     int threads = 256, grid = 1;    // CFL launches
+    bool small = true;              // every instance's offsets fit a 32-bit int
+    std::vector<int> direct;        // large instances: launched by themselves
     // per size class of the stage kernel: item range, shared memory, grid
     int cbeg[2] = {0, 0}, cend[2] = {0, 0}, cgrid[2] = {1, 1};
     size_t csmem[2] = {0, 0};
@@ -528,6 +530,11 @@ void batch_free(dg_batch *b)
     cudaFree(b->d_partials);
     delete b;
 }
+
+// Instances of at least this many nodes fill the GPU with their own launches
+// of the single-mesh stage kernels (inside the batch's step and graph); the
+// smaller ones share the persistent batched launches.
+constexpr long long kDirectDof = 1LL << 19;
 
 // Tile variant of order N inside a batch.  The batch runs every tile with one
 // block size (256 threads, 352 when a p = 6 instance is present), so the tile
@@ -573,14 +580,23 @@ cudaError_t batch_enqueue(const dg_batch *b, double cfl, int nsteps, cudaStream_
     cudaError_t e = cudaSuccess;
     int parity = 0;  // 0: the state is in Q
     for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
-        e = dg::batch_cfl(b->d_items, ni, b->d_inst, b->n, parity, cfl, b->d_err, b->grid,
-                          b->threads, s);
+        e = dg::batch_lambda(b->d_items, ni, b->d_inst, parity, b->d_err, b->grid, b->threads, s);
+        for (size_t k = 0; k < b->direct.size() && e == cudaSuccess; ++k) {
+            const dg::InstDev &I = b->inst[b->direct[k]];
+            e = dg::float_lambda(I.g, parity == 0 ? I.Q : I.Qt, I.lam_bits, b->d_err, s);
+        }
+        if (e == cudaSuccess) e = dg::batch_dt(b->d_inst, b->n, cfl, s);
         for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
             for (int c = 0; c < 2 && e == cudaSuccess; ++c)
                 if (b->cend[c] > b->cbeg[c])
                     e = dg::batch_stage(b->d_items + b->cbeg[c], b->cend[c] - b->cbeg[c],
                                         b->d_inst, parity, (float)kA[st], (float)kB[st], c,
-                                        b->cgrid[c], b->csmem[c], s);
+                                        b->small, b->cgrid[c], b->csmem[c], s);
+            for (size_t k = 0; k < b->direct.size() && e == cudaSuccess; ++k) {
+                const dg::InstDev &I = b->inst[b->direct[k]];
+                e = dg::float_stage(I.g, I.T, parity == 0 ? I.Q : I.Qt, parity == 0 ? I.Qt : I.Q,
+                                    I.dQ, (float)kA[st], (float)kB[st], I.dt, s);
+            }
             parity ^= 1;
         }
     }
@@ -653,6 +669,7 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
         }
         I.Qt = (float *)qt;
         b->dofs.push_back(g.E * N * N * N);
+        if ((long long)dg::NF * g.E * N * N * N > 0x7fffffffLL) b->small = false;
     }
     if (err == cudaSuccess) err = cudaMalloc((void **)&b->d_dt, sizeof(double) * n);
     if (err == cudaSuccess) err = cudaMalloc((void **)&b->d_lam, sizeof(unsigned long long) * n);
@@ -678,6 +695,10 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
             batch_free(b);
             return DG_ERR_UNSUPPORTED;
         }
+        if (b->dofs[i] >= kDirectDof) {  // fills the GPU by itself: own launches
+            b->direct.push_back(i);
+            continue;
+        }
         const int c = dg::batch_code_class(I.code);
         b->csmem[c] = std::max(b->csmem[c], sm);
         const long long nt = dg::tile_count(I.g, tx, ty);
@@ -686,10 +707,11 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
     std::stable_sort(b->items.begin(), b->items.end(),
                      [](const dg::BatchItem &x, const dg::BatchItem &y) { return x.code < y.code; });
     err = cudaMalloc((void **)&b->d_inst, sizeof(dg::InstDev) * n);
-    if (err == cudaSuccess) err = cudaMalloc((void **)&b->d_items, sizeof(dg::BatchItem) * b->items.size());
+    if (err == cudaSuccess && !b->items.empty())
+        err = cudaMalloc((void **)&b->d_items, sizeof(dg::BatchItem) * b->items.size());
     if (err == cudaSuccess)
         err = cudaMemcpy(b->d_inst, b->inst.data(), sizeof(dg::InstDev) * n, cudaMemcpyHostToDevice);
-    if (err == cudaSuccess)
+    if (err == cudaSuccess && !b->items.empty())
         err = cudaMemcpy(b->d_items, b->items.data(), sizeof(dg::BatchItem) * b->items.size(),
                          cudaMemcpyHostToDevice);
     if (err != cudaSuccess) {
@@ -711,10 +733,10 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
     for (int c = 0; c < 2; ++c) {
         const long long cnt = b->cend[c] - b->cbeg[c];
         if (cnt == 0) continue;
-        const long long per_sm = dg::batch_stage_blocks_per_sm(c, b->csmem[c]);
+        const long long per_sm = dg::batch_stage_blocks_per_sm(c, b->small, b->csmem[c]);
         b->cgrid[c] = (int)std::min<long long>((long long)sms * per_sm, cnt);
     }
-    b->grid = (int)std::min<long long>((long long)sms * 8, (long long)ni);
+    b->grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * 8, (long long)ni));
     *out = b;
     return DG_OK;
 }

@@ -396,14 +396,14 @@ __global__ void __launch_bounds__(FusedTile<N, TileShape<N, V>::TX, TileShape<N,
 // 64), class 1 the N = 7 tiles (343 nodes, 352 threads).
 // One tile of a batch, compiled as a separate function: each tile code keeps
 // its own register allocation instead of sharing the switch's worst case.
-template <int N, int V, int MODE>
+template <int N, int V, int MODE, typename Ix>
 __device__ __noinline__ void batched_tile(const float *__restrict__ Qin, float *__restrict__ Out,
                                           float *__restrict__ dQ, const Ops<float> &T,
                                           const Geo &g, long long tile, float A, float B,
                                           float dtr, unsigned char *smem)
 {
-    fused_tile<N, TileShape<N, V>::TX, TileShape<N, V>::TY, MODE>(Qin, Out, dQ, T, g, tile, A, B,
-                                                                   dtr, smem);
+    fused_tile<N, TileShape<N, V>::TX, TileShape<N, V>::TY, MODE, Ix>(Qin, Out, dQ, T, g, tile, A,
+                                                                       B, dtr, smem);
 }
 
 #define DG_FOR_EACH_CODE_C0(X) \
@@ -413,7 +413,8 @@ __device__ __noinline__ void batched_tile(const float *__restrict__ Qin, float *
 constexpr int kBatchClassThreads[2] = {256, 352};
 __host__ __device__ constexpr int batch_class(int code) { return (code >> 3) == 7 ? 1 : 0; }
 
-template <int MODE, int CLASS>
+// Ix: index type of every instance's arrays (int when all offsets fit).
+template <int MODE, int CLASS, typename Ix>
 __global__ void __launch_bounds__(CLASS == 0 ? 256 : 352, CLASS == 0 ? 4 : 2)
     batched_stage_kernel(const BatchItem *__restrict__ items, int nitems,
                          const InstDev *__restrict__ inst, int parity, float A, float B)
@@ -427,7 +428,7 @@ __global__ void __launch_bounds__(CLASS == 0 ? 256 : 352, CLASS == 0 ? 4 : 2)
         const float dtr = MODE != 0 ? (float)(*d.dt) : 0.0f;
 #define DG_CASE(NN, VV)                                                                       \
     case NN * 8 + VV:                                                                         \
-        batched_tile<NN, VV, MODE>(src, dst, d.dQ, d.T, d.g, item.tile, A, B, dtr, smem_raw); \
+        batched_tile<NN, VV, MODE, Ix>(src, dst, d.dQ, d.T, d.g, item.tile, A, B, dtr, smem_raw); \
         break;
         if constexpr (CLASS == 0) {
             switch (item.code) {

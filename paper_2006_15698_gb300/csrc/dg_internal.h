@@ -136,12 +136,29 @@ bool tile_code_info(int code, int *tx, int *ty, int *threads, size_t *smem);
 // size class of a tile code (0: N <= 6, 256 threads; 1: N = 7, 352 threads)
 int batch_code_class(int code);
 int batch_class_threads(int cls);
+// small: every instance's state offsets fit a 32-bit int (cheaper indexing)
 cudaError_t batch_stage(const BatchItem *items, int nitems, const InstDev *inst, int parity,
-                        float A, float B, int cls, int grid, size_t smem, cudaStream_t s);
+                        float A, float B, int cls, bool small, int grid, size_t smem,
+                        cudaStream_t s);
 // parity 0: the current state is in Q, 1: in the second state Qt
+// (nitems may be 0: then only the time steps are finalised from the Lambda
+// slots, which other launches may have filled)
 cudaError_t batch_cfl(const BatchItem *items, int nitems, const InstDev *inst, int ninst,
                       int parity, double cfl, int *err, int grid, int threads, cudaStream_t s);
-int batch_stage_blocks_per_sm(int cls, size_t smem);
+// the same in two halves: Lambda of the items' tiles, then dt of every instance
+cudaError_t batch_lambda(const BatchItem *items, int nitems, const InstDev *inst, int parity,
+                         int *err, int grid, int threads, cudaStream_t s);
+cudaError_t batch_dt(const InstDev *inst, int ninst, double cfl, cudaStream_t s);
+int batch_stage_blocks_per_sm(int cls, bool small, size_t smem);
+
+// Lambda (maximum wave-speed sum) of a float state merged into *lam_bits
+// (no time step yet), and one float-form RK stage of a single mesh
+// (src -> dst, dQ updated) with the degree's stage kernel: the launches of a
+// batch's large instances.
+cudaError_t float_lambda(const Geo &g, const float *Q, unsigned long long *lam_bits, int *err,
+                         cudaStream_t s);
+cudaError_t float_stage(const Geo &g, const Ops<float> &T, const float *src, float *dst, float *dQ,
+                        float A, float B, const double *dt, cudaStream_t s);
 
 // Launchers implemented per scalar type (dg_kernels_f64.cu / dg_kernels_f32.cu).
 // Each returns cudaSuccess or the launch error.

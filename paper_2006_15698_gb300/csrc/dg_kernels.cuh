@@ -1027,6 +1027,21 @@ cudaError_t rk_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, const doub
     }
 }
 
+// One float-form RK stage (MODE 1) of a single mesh from src to dst with the
+// stage kernel of the degree's table entry: the batch's launch path for
+// instances large enough to fill the GPU by themselves.
+template <int N, typename real>
+cudaError_t stage_n(const Geo &g, const Ops<real> &T, const real *src, real *dst, real *dQ,
+                    real A, real B, const double *dt, cudaStream_t s)
+{
+    if constexpr (std::is_same<real, float>::value) {
+        return column_stage(N) ? launch_column<N, 1>(g, T, src, dst, dQ, A, B, dt, nullptr, s)
+                               : launch_fused<N, 1>(g, T, src, dst, dQ, A, B, dt, nullptr, s);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
 // host table of the quadrature weight of every in-element node
 inline NodeWeights node_weights(const Geo &g)
 {
@@ -1182,7 +1197,9 @@ cudaError_t advance_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, doubl
     KW cudaError_t rk_n<NN, REAL>(const Geo &, const Ops<REAL> &, REAL *, REAL *,             \
                                   const double *, Work &, cudaStream_t, bool);               \
     KW cudaError_t advance_n<NN, REAL>(const Geo &, const Ops<REAL> &, REAL *, REAL *, double, \
-                                       int, double *, double *, Work &, cudaStream_t);
+                                       int, double *, double *, Work &, cudaStream_t);       \
+    KW cudaError_t stage_n<NN, REAL>(const Geo &, const Ops<REAL> &, const REAL *, REAL *,     \
+                                     REAL *, REAL, REAL, const double *, cudaStream_t);
 
 template <typename real>
 cudaError_t Launch<real>::advance(const Geo &g, const Ops<real> &T, real *Q, real *dQ, double cfl,

@@ -162,3 +162,41 @@ def test_batch_rejects_bad_specs(dgm):
         dg.Batch([dict(nx=2, ny=2, nz=2, p=7)])
     with pytest.raises(dg.DGError):
         dg.Batch([dict(nx=0, ny=2, nz=2, p=1)])
+
+
+@pytest.mark.parametrize("kernel", ["column", "tile"])
+def test_hybrid_batch_large_instances_match_single_meshes(dgm, kernel):
+    """Instances of at least 2^19 nodes run the single-mesh stage kernels as
+    launches of their own inside the batch's step (and graph); each still
+    equals the same mesh stepped alone, bit for bit, next to small instances
+    that share the persistent launch."""
+    dg = dgm
+    import torch
+    for p in range(0, 7):
+        dg.dg_set_stage_kernel(p, dg.DG_STAGE_COLUMN if kernel == "column" else dg.DG_STAGE_TILE)
+    specs = [dict(nx=24, ny=24, nz=24, p=3, Lx=10.0, Ly=10.0, Lz=10.0),   # 884,736 nodes: own launches
+             dict(nx=5, ny=6, nz=5, p=2, Lx=10.0, Ly=10.0, Lz=10.0),
+             dict(nx=12, ny=10, nz=9, p=5, Lx=10.0, Ly=10.0, Lz=10.0),    # 233,280 nodes: shared
+             dict(nx=20, ny=20, nz=12, p=4, Lx=10.0, Ly=10.0, Lz=10.0)]   # 600,000 nodes: own launches
+    batch = dg.Batch(specs)
+    for i in range(len(specs)):
+        batch.init(i, "vortex", inputs.vortex_params(200 + i, BOX))
+    singles = []
+    for i, sp in enumerate(specs):
+        m = dg.Mesh(sp["nx"], sp["ny"], sp["nz"], sp["p"], *BOX, precision=dg.DG_FP32)
+        Q = batch.Q[i].clone()
+        singles.append((m, Q, torch.zeros_like(Q), torch.zeros(1, dtype=torch.float64, device="cuda")))
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for use_graph in (False, True, True):
+            batch.step(0.5, use_graph=use_graph)
+            for m, Q, dQ, dt in singles:
+                m.cfl_dt(Q, 0.5, dt)
+                m.rk_step(Q, dQ, dt)
+    torch.cuda.synchronize()
+    dts = batch.dts()
+    for i, (m, Q, dQ, dt) in enumerate(singles):
+        assert dts[i] == float(dt.item()), i
+        assert torch.equal(batch.Q[i], Q), (i, specs[i])
+    assert batch.last_error() == dg.DG_OK
