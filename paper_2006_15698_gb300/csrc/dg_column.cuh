@@ -77,16 +77,37 @@ struct ColTile {
     static constexpr int XT = (TX + 1) * TY * N2, YT = (TY + 1) * TX * N2, ZT = EPB * N2;
 };
 
+// Packed float pairs: one FFMA2 / FMUL2 / FADD2 instruction does two
+// independent IEEE operations (sm_100 and later), so paired work issues half
+// the floating-point instructions with the same rounding per lane.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
 // Trace sum_c l[c] v(c) of a node line, with the same explicitly ordered
 // operations for every source (shared or global memory), so that two columns
-// computing the same trace get the same float.
+// computing the same trace get the same float: even and odd nodes summed in
+// the two lanes of a packed pair, then added.
 template <int N>
 __device__ __forceinline__ float line_dot(const float *l, const float v[N])
 {
-    float s = __fmul_rn(l[0], v[0]);
+    if constexpr (N == 1) {
+        return __fmul_rn(l[0], v[0]);
+    } else {
+        float2 s = __fmul2_rn(f2(l[0], l[1]), f2(v[0], v[1]));
 #pragma unroll
-    for (int c = 1; c < N; ++c) s = __fmaf_rn(l[c], v[c], s);
-    return s;
+        for (int c = 2; c + 1 < N; c += 2) s = __ffma2_rn(f2(l[c], l[c + 1]), f2(v[c], v[c + 1]), s);
+        if constexpr (N % 2 == 1) s.x = __fmaf_rn(l[N - 1], v[N - 1], s.x);
+        return __fadd_rn(s.x, s.y);
+    }
+}
+
+// acc + sum_c d[c] v[c] into a packed accumulator (even c in .x, odd in .y)
+template <int N>
+__device__ __forceinline__ float2 dot2_acc(const float d[N], const float v[N], float2 acc)
+{
+#pragma unroll
+    for (int c = 0; c + 1 < N; c += 2) acc = __ffma2_rn(f2(d[c], d[c + 1]), f2(v[c], v[c + 1]), acc);
+    if constexpr (N % 2 == 1) acc.x = __fmaf_rn(d[N - 1], v[N - 1], acc.x);
+    return acc;
 }
 
 template <int N, int DIR>
@@ -123,17 +144,34 @@ __device__ __forceinline__ void global_trace(const float *__restrict__ Q, Ix E, 
     }
 }
 
-// 2 F* of the local Lax-Friedrichs flux through a face with normal +e_DIR
+// 2 F* of the local Lax-Friedrichs flux through a face with normal +e_DIR:
+// the two sides' pressure, normal velocity, flux and speed evaluated as
+// packed pairs (left in .x, right in .y), every operation explicitly rounded.
 template <int DIR>
 __device__ __forceinline__ void lf_flux2_f(const float qL[NF], const float qR[NF], float gamma,
                                            float gm1, float f[NF])
 {
-    float fL[NF], fR[NF], sL, sR;
-    normal_flux_f<DIR>(qL, gamma, gm1, fL, sL);
-    normal_flux_f<DIR>(qR, gamma, gm1, fR, sR);
-    const float lam = fmaxf(sL, sR);
+    float2 q[NF];
 #pragma unroll
-    for (int n = 0; n < NF; ++n) f[n] = (fL[n] + fR[n]) - lam * (qR[n] - qL[n]);
+    for (int n = 0; n < NF; ++n) q[n] = f2(qL[n], qR[n]);
+    const float2 rinv = f2(fast_rcp(qL[0]), fast_rcp(qR[0]));
+    float2 mm = __fmul2_rn(q[1], q[1]);
+    mm = __ffma2_rn(q[2], q[2], mm);
+    mm = __ffma2_rn(q[3], q[3], mm);
+    // p = (gamma - 1) (E - |m|^2 / (2 rho))
+    const float2 p = __fmul2_rn(f2(gm1, gm1), __ffma2_rn(f2(-0.5f, -0.5f), __fmul2_rn(mm, rinv), q[4]));
+    const float2 un = __fmul2_rn(q[1 + DIR], rinv);
+    const float2 c2 = __fmul2_rn(__fmul2_rn(f2(gamma, gamma), p), rinv);
+    const float lam = fmaxf(__fadd_rn(fabsf(un.x), fast_sqrt(c2.x)),
+                            __fadd_rn(fabsf(un.y), fast_sqrt(c2.y)));
+    float2 F[NF];
+    F[0] = q[1 + DIR];
+#pragma unroll
+    for (int n = 1; n < 4; ++n) F[n] = n == DIR + 1 ? __ffma2_rn(q[n], un, p) : __fmul2_rn(q[n], un);
+    F[4] = __fmul2_rn(__fadd2_rn(q[4], p), un);
+#pragma unroll
+    for (int n = 0; n < NF; ++n)
+        f[n] = __fmaf_rn(-lam, __fsub_rn(qR[n], qL[n]), __fadd_rn(F[n].x, F[n].y));
 }
 
 // Copy layer zl (periodic) of the column into a slot: whole valid rows.
@@ -424,20 +462,18 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
                 load_line<N>(f + 0 * NF * N3 + n * N3 + (k * N + j) * N, vx);
                 load_line<N>(f + 1 * NF * N3 + n * N3 + (k * N + i) * N, vy);
                 load_line<N>(f + 2 * NF * N3 + n * N3 + (j * N + i) * N, vz);
-                float acc = 0.0f;
-#pragma unroll
-                for (int c = 0; c < N; ++c) acc = __fmaf_rn(dx[c], vx[c], acc);
-#pragma unroll
-                for (int c = 0; c < N; ++c) acc = __fmaf_rn(dy[c], vy[c], acc);
-#pragma unroll
-                for (int c = 0; c < N; ++c) acc = __fmaf_rn(dz[c], vz[c], acc);
+                // packed pairs, explicitly rounded: every instantiation (rhs,
+                // stage, dQ-only last stage) gives the same floats
+                float2 a2 = f2(0.0f, 0.0f);
+                a2 = dot2_acc<N>(dx, vx, a2);
+                a2 = dot2_acc<N>(dy, vy, a2);
+                a2 = dot2_acc<N>(dz, vz, a2);
                 const float2 hx = *reinterpret_cast<const float2 *>(h + ((0 * NF + n) * N2 + px) * 2);
                 const float2 hy = *reinterpret_cast<const float2 *>(h + ((1 * NF + n) * N2 + py) * 2);
-                // explicitly rounded: every instantiation (rhs, stage, dQ-only
-                // last stage) gives the same floats
-                acc = __fmaf_rn(-lpx, hx.y, __fmaf_rn(lmx, hx.x, acc));
-                acc = __fmaf_rn(-lpy, hy.y, __fmaf_rn(lmy, hy.x, acc));
-                acc = __fmaf_rn(-lpz, zp[n * N2 + pz], __fmaf_rn(lmz, zm[n * N2 + pz], acc));
+                a2 = __ffma2_rn(f2(lmx, -lpx), hx, a2);
+                a2 = __ffma2_rn(f2(lmy, -lpy), hy, a2);
+                a2 = __ffma2_rn(f2(lmz, -lpz), f2(zm[n * N2 + pz], zp[n * N2 + pz]), a2);
+                const float acc = __fadd_rn(a2.x, a2.y);
                 const Ix o = ((Ix)n * E + e) * N3 + node;
                 if (MODE == 0) {
                     Out[o] = acc;
