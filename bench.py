@@ -49,6 +49,14 @@ WORKLOADS = {
                             init="vortex", params=None, prec="fp64", cfl=0.5,
                             desc="isentropic vortex (seed 0), [0,10]^3, 8^3 elements, p=3, FP64"),
 }
+# roofline curves: Taylor-Green at p = 1..6, about 30 M DOF each, both precisions
+for _p, _n in ((1, 155), (2, 104), (3, 78), (4, 62), (5, 52), (6, 44)):
+    for _prec in ("fp64", "fp32"):
+        WORKLOADS[f"tgv_p{_p}_30m_{_prec}"] = dict(
+            nel=(_n, _n, _n), p=_p, box=(0, 0, 0, TWO_PI, TWO_PI, TWO_PI), init="tgv",
+            params=[1.0, 1.0, 0.1], prec=_prec, cfl=0.5,
+            desc=f"Taylor-Green vortex, Mach 0.1, {_n}^3 elements, p={_p} "
+                 f"({_n ** 3 * (_p + 1) ** 3 / 1e6:.1f} M DOF), {_prec.upper()} (roofline curve over p)")
 WORKLOADS["batch256_fp32"] = dict(
     kind="batch", count=256, nrange=(4, 32), prange=(1, 5), seed=0, prec="fp32", cfl=0.5,
     box=(0, 0, 0, 10.0, 10.0, 10.0), p=3, nel=(1, 1, 1), init="vortex", params=None,

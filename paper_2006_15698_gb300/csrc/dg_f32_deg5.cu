@@ -1,0 +1,7 @@
+// Float-form stage paths of polynomial degree 5 (N = p + 1 = 6),
+// compiled apart from the other degrees so that the builds run in parallel.
+#include "dg_kernels.cuh"
+
+namespace dg {
+DG_INSTANTIATE_N(template, 6, float)
+}
