@@ -1,5 +1,6 @@
-"""Parity at the full size of the headline workload (Taylor-Green vortex,
-64^3 elements, p = 4, FP64), in the launch configuration bench.py times.
+"""Parity at the full size of the bench workloads (Taylor-Green vortex,
+64^3 elements, p = 4, FP64; isentropic vortex, 128^3 elements, p = 3, FP32),
+in the launch configuration bench.py times (dg_advance).
 
 The oracle cannot evaluate the whole mesh quickly, so the right-hand side is
 compared on a sample of elements (including every kind of periodic wrap),
@@ -88,4 +89,62 @@ def test_rk_step_conserves_and_is_consistent(full):
     d = Q1 - Q
     rel = np.linalg.norm(d - dt * R) / np.linalg.norm(dt * R)
     assert rel < 0.05, rel
+    assert m.last_error() == dg.DG_OK
+
+
+def test_advance_full_fp64_equals_separate_calls(full):
+    """The bench's launch path (dg_advance, two steps) on the full headline
+    mesh: bitwise the separate cfl/rk/norms calls; the first time step is the
+    oracle's bit for bit; the integrals are conserved across the steps."""
+    dg, om, m, Q = full
+    import torch
+    Qa, Qb = to_dev(Q), to_dev(Q)
+    dQa, dQb = torch.zeros_like(Qa), torch.zeros_like(Qb)
+    dts_a, integ_a = [], []
+    for _ in range(2):
+        dt = m.cfl_dt(Qa, 0.5)
+        m.rk_step(Qa, dQa, dt)
+        dts_a.append(dt.clone())
+        integ_a.append(m.norms(Qa).clone())
+    dts_b, integ_b = m.advance(Qb, dQb, 0.5, 2)
+    torch.cuda.synchronize()
+    assert torch.equal(torch.cat(dts_a), dts_b)
+    assert torch.equal(torch.stack(integ_a), integ_b)
+    assert torch.equal(Qa, Qb)
+    assert float(dts_b[0].item()) == om.cfl_dt(Q, 0.5)[0]
+    I0 = to_host(m.norms(to_dev(Q)))
+    I2 = to_host(integ_b)[1]
+    absI = om.norms(np.abs(Q))[:5]
+    scale = np.maximum(absI, 1e-3 * absI.max())
+    assert np.max(np.abs(I2[:5] - I0[:5]) / scale) < 1e-13
+    assert m.last_error() == dg.DG_OK
+
+
+def test_advance_full_fp32_vortex128():
+    """The FP32 bench configuration (isentropic vortex, 128^3 elements, p = 3)
+    through dg_advance: bitwise the separate calls (whose last stage and
+    copy-back the step epilogue replaces), finite, and the five integrals
+    conserved to float rounding."""
+    dg = dg_module()
+    import torch
+    L = 16.0
+    box = (0.0, 0.0, 0.0, L, L, L)
+    m = dg.Mesh(128, 128, 128, 3, *box, precision=dg.DG_FP32)
+    Q0 = m.init("vortex", inputs.vortex_params(0, box))
+    Qa, Qb = Q0.clone(), Q0.clone()
+    dQa, dQb = torch.zeros_like(Qa), torch.zeros_like(Qb)
+    dt = m.cfl_dt(Qa, 0.5)
+    m.rk_step(Qa, dQa, dt)
+    integ_a = m.norms(Qa)
+    dts_b, integ_b = m.advance(Qb, dQb, 0.5, 1)
+    torch.cuda.synchronize()
+    assert torch.equal(dt, dts_b)
+    assert torch.equal(Qa, Qb)
+    assert torch.equal(integ_a, integ_b[0])
+    assert bool(torch.isfinite(Qb).all())
+    I0 = to_host(m.norms(Q0))
+    I1 = to_host(integ_b)[0]
+    absI = to_host(m.norms(Q0.abs()))
+    scale = np.maximum(absI[:5], 1e-3 * absI[:5].max())
+    assert np.max(np.abs(I1[:5] - I0[:5]) / scale) < 1e-6
     assert m.last_error() == dg.DG_OK
