@@ -57,9 +57,14 @@ struct ColTile {
     static constexpr int EPB = TX * TY;
     static constexpr int THREADS = ((EPB * N3 + 31) / 32) * 32;
     static constexpr int pad16(int x) { return x + ((16 - x % 32) + 32) % 32; }
-    // one layer's state [NF][EPB][N3] (rows of TX elements contiguous, as in
-    // DRAM, so whole rows are copied); 16-byte aligned slots
-    static constexpr int QSLOT = ((NF * EPB * N3 + 3) / 4) * 4;
+    // one layer's state [NF][EPB][ESTR] (element rows in DRAM order); 16-byte
+    // aligned slots
+    // element stride inside a slot: N^3 padded by 16 floats when N^3 is a
+    // multiple of 32, so that two elements' nodes fall into different bank
+    // halves (the strided y/z node-line loads of neighbouring elements would
+    // otherwise collide); the per-thread cp.async places each unit anyway
+    static constexpr int ESTR = N3 % 32 == 0 ? N3 + 16 : N3;
+    static constexpr int QSLOT = ((NF * EPB * ESTR + 3) / 4) * 4;
     static constexpr int FSTR = pad16(3 * NF * N3);      // fluxes [3][NF][N3], direction-major
     static constexpr int TSTR = pad16(6 * NF * N2);      // traces [face = 2 dir + side][NF][N2]
     static constexpr int HSTR = pad16(2 * NF * N2 * 2);  // x, y face fluxes [2][NF][N2][(-,+)]
@@ -191,7 +196,8 @@ __device__ __forceinline__ void column_prefetch(const float *__restrict__ Q, flo
         if (b >= tyv || u * W >= txv * N3) continue;
         const Ix e0 = ex0 + (Ix)g.nx * (ey0 + b) + plane * zl;
         const float *src = Q + ((Ix)n * (Ix)g.E + e0) * N3 + u * W;
-        float *dst = slot + (n * EPB + b * TX) * N3 + u * W;
+        const int a = (u * W) / N3, o = u * W - a * N3;  // element of the row, node offset
+        float *dst = slot + (n * EPB + b * TX + a) * CT::ESTR + o;
         if constexpr (W == 4) cp_async16(dst, src);
         else cp_async4(dst, src);
     }
@@ -212,7 +218,7 @@ __device__ __forceinline__ void line_task(const float *slot, float *sT, const fl
 #pragma unroll
     for (int n = 0; n < NF; ++n) {
         float v[N];
-        line_values<N, DIR>(slot + (n * EPB + el) * N3 + base, v);
+        line_values<N, DIR>(slot + (n * EPB + el) * CT::ESTR + base, v);
         if (which != 1) t[((2 * DIR + 0) * NF + n) * N2 + ln] = line_dot<N>(lm, v);
         if (which != 0) t[((2 * DIR + 1) * NF + n) * N2 + ln] = line_dot<N>(lp, v);
     }
@@ -370,7 +376,7 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
             }
             float q[NF];
 #pragma unroll
-            for (int n = 0; n < NF; ++n) q[n] = cur[(n * EPB + el) * N3 + node];
+            for (int n = 0; n < NF; ++n) q[n] = cur[(n * EPB + el) * CT::ESTR + node];
             const float rinv = fast_rcp(q[0]);
             const float u = q[1] * rinv, v = q[2] * rinv, w = q[3] * rinv;
             const float p = gm1 * (q[4] - 0.5f * (q[1] * u + q[2] * v + q[3] * w));
@@ -480,7 +486,7 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
                 } else {
                     const float d = __fmaf_rn(dtr, acc, A == 0.0f ? 0.0f : __fmul_rn(A, dq[n]));
                     dQ[o] = d;
-                    if (MODE == 1) Out[o] = __fmaf_rn(B, d, cur[(n * EPB + el) * N3 + node]);
+                    if (MODE == 1) Out[o] = __fmaf_rn(B, d, cur[(n * EPB + el) * CT::ESTR + node]);
                 }
             }
         }
