@@ -920,22 +920,29 @@ cudaError_t launch_column_ix(const Geo &g, const Ops<float> &T, const float *Qin
 {
     using SH = ColShape<N, 0>;
     using CT = ColTile<N, SH::TX, SH::TY>;
-    static int resident = 0;  // CTAs of this kernel resident on the device at once
+    // CTAs of this kernel resident on a device at once, per device (a benign
+    // race: concurrent first calls store the same value)
+    constexpr int kDevices = 64;
+    static int resident_of[kDevices] = {};
     if (CT::BYTES > 48 * 1024) {
         cudaError_t err = cudaFuncSetAttribute(column_stage_kernel<N, 0, MODE, Ix>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)CT::BYTES);
         if (err != cudaSuccess) return err;
     }
+    int dev = 0;
+    cudaError_t derr = cudaGetDevice(&dev);
+    if (derr != cudaSuccess) return derr;
+    int resident = dev < kDevices ? resident_of[dev] : 0;
     if (resident == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaError_t err = cudaGetDevice(&dev);
-        if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int sms = 0, per_sm = 0;
+        cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (err == cudaSuccess)
             err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                 &per_sm, column_stage_kernel<N, 0, MODE, Ix>, CT::THREADS, CT::BYTES);
         if (err != cudaSuccess) return err;
         resident = sms * (per_sm > 0 ? per_sm : 1);
+        if (dev < kDevices) resident_of[dev] = resident;
     }
     const long long ncols =
         (long long)((g.nx + SH::TX - 1) / SH::TX) * ((g.ny + SH::TY - 1) / SH::TY);
