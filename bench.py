@@ -321,7 +321,7 @@ def _dist():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for f in ("dg_kernels.cuh", "dg_fused.cuh", "dg_column.cuh"):
+    for f in ("dg_kernels.cuh", "dg_fused.cuh", "dg_column.cuh", "dg_lines.cuh"):
         with open(os.path.join(ROOT, "paper_2006_15698_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

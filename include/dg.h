@@ -232,11 +232,14 @@ int dg_get_tile_variant(int p);
  *   DG_STAGE_COLUMN  one CTA per column of elements, walking up a chunk of z
  *                    layers with the next layers prefetched into shared
  *                    memory (cp.async); every z interface computed once
- * Both give the same right-hand side up to float rounding order.
+ *   DG_STAGE_LINES   the same column walk with one thread per z node line:
+ *                    z fluxes, z traces and z interface fluxes stay in
+ *                    registers; the same floats as DG_STAGE_COLUMN
+ * All give the same right-hand side up to float rounding order.
  *   dg_set_stage_kernel  DG_ERR_UNSUPPORTED for p outside [0, DG_MAX_P],
  *                        DG_ERR_ARG for an unknown kind
- *   dg_get_stage_kernel  the kind (-1 if p unsupported); default DG_STAGE_COLUMN */
-enum { DG_STAGE_TILE = 0, DG_STAGE_COLUMN = 1 };
+ *   dg_get_stage_kernel  the kind (-1 if p unsupported); default DG_STAGE_LINES */
+enum { DG_STAGE_TILE = 0, DG_STAGE_COLUMN = 1, DG_STAGE_LINES = 2 };
 dg_status dg_set_stage_kernel(int p, int kind);
 int dg_get_stage_kernel(int p);
 

@@ -3,12 +3,14 @@
 For every polynomial degree it times one LSERK45 step of a representative
 float mesh (isentropic vortex, about `target_dof` nodes) with each tile
 variant the library offers (dg_tile_variant_count / dg_tile_shape) and with
-the column kernel, and writes the table that ``dg.load_tuning`` reads: the
+the two column kernels (one thread per node, "column"; one thread per z node
+line, "lines"), and writes the table that ``dg.load_tuning`` reads: the
 fastest tile variant (used by batches, and by single meshes when "kernel" is
-"tile") and the faster single-mesh kernel:
+"tile") and the fastest single-mesh kernel:
 
-    {"gpu": ..., "degrees": {"3": {"variant": 1, "tile": [2, 2], "kernel": "column",
-                                   "ms_per_step": {"0": 5.1, "1": 4.8, "column": 4.1}}, ...}}
+    {"gpu": ..., "degrees": {"3": {"variant": 1, "tile": [2, 2], "kernel": "lines",
+                                   "ms_per_step": {"0": 5.1, "1": 4.8, "column": 4.1,
+                                                   "lines": 3.5}}, ...}}
 
 Run on the GPU the library will serve:
     python -m paper_2006_15698_gb300.autotune [--out PATH] [--degrees 1,2,3]
@@ -26,9 +28,9 @@ from . import dg, inputs
 def time_variant(p, variant, target_dof=8e6, steps=6, warmup=2):
     """Milliseconds per LSERK45 step (CFL + 5 stages) of a float vortex mesh
     of about target_dof nodes at degree p with the given tile variant, or
-    with the column kernel for variant "column"."""
-    if variant == "column":
-        dg.dg_set_stage_kernel(p, dg.DG_STAGE_COLUMN)
+    with a column kernel for variant "column" or "lines"."""
+    if variant in ("column", "lines"):
+        dg.dg_set_stage_kernel(p, dg.STAGE_KINDS[variant])
     else:
         dg.dg_set_stage_kernel(p, dg.DG_STAGE_TILE)
         dg.dg_set_tile_variant(p, variant)
@@ -59,12 +61,13 @@ def tune(degrees=(1, 2, 3, 4, 5, 6), target_dof=8e6, steps=6):
         nv = dg.dg_tile_variant_count(p)
         times = {v: time_variant(p, v, target_dof, steps) for v in range(nv)}
         best = min(times, key=times.get)
-        t_col = time_variant(p, "column", target_dof, steps)
-        kernel = "column" if t_col < times[best] else "tile"
-        dg.dg_set_tile_variant(p, best)
-        dg.dg_set_stage_kernel(p, dg.DG_STAGE_COLUMN if kernel == "column" else dg.DG_STAGE_TILE)
         ms = {str(v): t for v, t in times.items()}
-        ms["column"] = t_col
+        for kind in ("column", "lines"):
+            ms[kind] = time_variant(p, kind, target_dof, steps)
+        kernel = min(("tile", "column", "lines"),
+                     key=lambda k: times[best] if k == "tile" else ms[k])
+        dg.dg_set_tile_variant(p, best)
+        dg.dg_set_stage_kernel(p, dg.STAGE_KINDS[kernel])
         table["degrees"][str(p)] = {"variant": best, "tile": list(dg.dg_tile_shape(p, best)),
                                     "kernel": kernel, "ms_per_step": ms}
     return table

@@ -438,9 +438,13 @@ dg_status dg_rhs_static(int nx, int ny, int nz, int p, double x0, double y0, dou
 // ---------------------------------------------------------------------------
 namespace dg {
 static int g_tile_var[NMAX + 1] = {0, 0, 0, 0, 0, 0, 0, 0};
-static int g_stage_kind[NMAX + 1] = {1, 1, 1, 1, 1, 1, 1, 1};
+static int g_stage_kind[NMAX + 1] = {2, 2, 2, 2, 2, 2, 2, 2};
 int tile_variant(int N) { return (N >= 1 && N <= NMAX) ? g_tile_var[N] : 0; }
-bool column_stage(int N) { return N >= 1 && N <= NMAX && g_stage_kind[N] == DG_STAGE_COLUMN; }
+bool column_stage(int N)
+{
+    return N >= 1 && N <= NMAX && (g_stage_kind[N] == DG_STAGE_COLUMN || g_stage_kind[N] == DG_STAGE_LINES);
+}
+bool line_stage(int N) { return N >= 1 && N <= NMAX && g_stage_kind[N] == DG_STAGE_LINES; }
 }  // namespace dg
 
 extern "C" {
@@ -467,7 +471,8 @@ int dg_get_tile_variant(int p) { return (p < 0 || p > DG_MAX_P) ? -1 : dg::g_til
 dg_status dg_set_stage_kernel(int p, int kind)
 {
     if (p < 0 || p > DG_MAX_P) return DG_ERR_UNSUPPORTED;
-    if (kind != DG_STAGE_TILE && kind != DG_STAGE_COLUMN) return DG_ERR_ARG;
+    if (kind != DG_STAGE_TILE && kind != DG_STAGE_COLUMN && kind != DG_STAGE_LINES)
+        return DG_ERR_ARG;
     dg::g_stage_kind[p + 1] = kind;
     return DG_OK;
 }

@@ -179,6 +179,33 @@ __device__ __forceinline__ void lf_flux2_f(const float qL[NF], const float qR[NF
         f[n] = __fmaf_rn(-lam, __fsub_rn(qR[n], qL[n]), __fadd_rn(F[n].x, F[n].y));
 }
 
+// Euler fluxes of one node (Eq. 2-3) in the three directions, every
+// operation explicitly rounded so that the column kernels agree bitwise.
+__device__ __forceinline__ void node_flux_f(const float q[NF], float gm1, float fx[NF],
+                                            float fy[NF], float fz[NF])
+{
+    const float rinv = fast_rcp(q[0]);
+    const float u = __fmul_rn(q[1], rinv), v = __fmul_rn(q[2], rinv), w = __fmul_rn(q[3], rinv);
+    const float m2 = __fmaf_rn(q[3], w, __fmaf_rn(q[2], v, __fmul_rn(q[1], u)));
+    const float p = __fmul_rn(gm1, __fmaf_rn(-0.5f, m2, q[4]));
+    const float ep = __fadd_rn(q[4], p);
+    fx[0] = q[1];
+    fx[1] = __fmaf_rn(q[1], u, p);
+    fx[2] = __fmul_rn(q[2], u);
+    fx[3] = __fmul_rn(q[3], u);
+    fx[4] = __fmul_rn(ep, u);
+    fy[0] = q[2];
+    fy[1] = __fmul_rn(q[1], v);
+    fy[2] = __fmaf_rn(q[2], v, p);
+    fy[3] = __fmul_rn(q[3], v);
+    fy[4] = __fmul_rn(ep, v);
+    fz[0] = q[3];
+    fz[1] = __fmul_rn(q[1], w);
+    fz[2] = __fmul_rn(q[2], w);
+    fz[3] = __fmaf_rn(q[3], w, p);
+    fz[4] = __fmul_rn(ep, w);
+}
+
 // Copy layer zl (periodic) of the column into a slot: whole valid rows.
 template <int N, int TX, int TY, typename Ix>
 __device__ __forceinline__ void column_prefetch(const float *__restrict__ Q, float *slot,
@@ -377,28 +404,17 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
             float q[NF];
 #pragma unroll
             for (int n = 0; n < NF; ++n) q[n] = cur[(n * EPB + el) * CT::ESTR + node];
-            const float rinv = fast_rcp(q[0]);
-            const float u = q[1] * rinv, v = q[2] * rinv, w = q[3] * rinv;
-            const float p = gm1 * (q[4] - 0.5f * (q[1] * u + q[2] * v + q[3] * w));
-            const float ep = q[4] + p;
+            float fx[NF], fy[NF], fz[NF];
+            node_flux_f(q, gm1, fx, fy, fz);
             float *sx = sF + (size_t)el * FSTR + 0 * NF * N3 + (k * N + j) * N + i;
             float *sy = sF + (size_t)el * FSTR + 1 * NF * N3 + (k * N + i) * N + j;
             float *sz = sF + (size_t)el * FSTR + 2 * NF * N3 + (j * N + i) * N + k;
-            sx[0 * N3] = q[1];
-            sx[1 * N3] = q[1] * u + p;
-            sx[2 * N3] = q[2] * u;
-            sx[3 * N3] = q[3] * u;
-            sx[4 * N3] = ep * u;
-            sy[0 * N3] = q[2];
-            sy[1 * N3] = q[1] * v;
-            sy[2 * N3] = q[2] * v + p;
-            sy[3 * N3] = q[3] * v;
-            sy[4 * N3] = ep * v;
-            sz[0 * N3] = q[3];
-            sz[1 * N3] = q[1] * w;
-            sz[2 * N3] = q[2] * w;
-            sz[3 * N3] = q[3] * w + p;
-            sz[4 * N3] = ep * w;
+#pragma unroll
+            for (int n = 0; n < NF; ++n) {
+                sx[n * N3] = fx[n];
+                sy[n * N3] = fy[n];
+                sz[n * N3] = fz[n];
+            }
         }
         for (int t = tid; t < CT::LINE_TASKS; t += nthr) {
             const int w = t / (EPB * N2), r = t - w * (EPB * N2);

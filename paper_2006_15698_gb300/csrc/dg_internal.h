@@ -100,7 +100,8 @@ constexpr int kNormBlocks = 1024;  // fixed partition of the norms reduction
 // tuning table, set through dg_set_tile_variant; read at each launch).
 int tile_variant(int N);
 // true when the single-mesh float stage of order N uses the column kernel
-bool column_stage(int N);
+bool column_stage(int N);  // a column kernel (column or line form) runs the stage
+bool line_stage(int N);    // ... and it is the line form
 
 // tiles of TX x TY elements covering a mesh: ceil(nx/TX) x ceil(ny/TY) x nz
 __host__ __device__ inline long long tile_count(const Geo &g, int TX, int TY)

@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
 
 #include "dg_fused.cuh"
 #include "dg_column.cuh"
+#include "dg_lines.cuh"
 
 // ---------------------------------------------------------------------------
 // time step, integrals, initial states
@@ -910,24 +911,27 @@ cudaError_t launch_fused(const Geo &g, const Ops<float> &T, const float *Qin, fl
     return launch_fused_v<N, 0, MODE>(g, T, Qin, Out, dQ, A, B, dt, prof, s);
 }
 
-// Column kernel launch: the z range of every column is cut into chunks so
-// that the number of CTAs fills the GPU's resident slots in whole waves
-// (time ~ waves x (layers per chunk + the chunk's extra prologue layer)).
-template <int N, int MODE, typename Ix>
+// Column kernel launch (LINES: line_stage_kernel, else column_stage_kernel):
+// the z range of every column is cut into chunks so that the number of CTAs
+// fills the GPU's resident slots in whole waves (time ~ waves x (layers per
+// chunk + the chunk's extra prologue layer)).
+template <int N, int MODE, typename Ix, bool LINES>
 cudaError_t launch_column_ix(const Geo &g, const Ops<float> &T, const float *Qin, float *Out,
                              float *dQ, float A, float B, const double *dt, Prof *prof,
                              cudaStream_t s)
 {
-    using SH = ColShape<N, 0>;
-    using CT = ColTile<N, SH::TX, SH::TY>;
+    constexpr int TX = LINES ? LineShape<N, 0>::TX : ColShape<N, 0>::TX;
+    constexpr int TY = LINES ? LineShape<N, 0>::TY : ColShape<N, 0>::TY;
+    constexpr int THREADS = LINES ? LineTile<N, TX, TY>::THREADS : ColTile<N, TX, TY>::THREADS;
+    constexpr size_t BYTES = LINES ? LineTile<N, TX, TY>::BYTES : ColTile<N, TX, TY>::BYTES;
+    auto kernel = LINES ? line_stage_kernel<N, 0, MODE, Ix> : column_stage_kernel<N, 0, MODE, Ix>;
     // CTAs of this kernel resident on a device at once, per device (a benign
     // race: concurrent first calls store the same value)
     constexpr int kDevices = 64;
     static int resident_of[kDevices] = {};
-    if (CT::BYTES > 48 * 1024) {
-        cudaError_t err = cudaFuncSetAttribute(column_stage_kernel<N, 0, MODE, Ix>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)CT::BYTES);
+    if (BYTES > 48 * 1024) {
+        cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)BYTES);
         if (err != cudaSuccess) return err;
     }
     int dev = 0;
@@ -938,14 +942,12 @@ cudaError_t launch_column_ix(const Geo &g, const Ops<float> &T, const float *Qin
         int sms = 0, per_sm = 0;
         cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (err == cudaSuccess)
-            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, column_stage_kernel<N, 0, MODE, Ix>, CT::THREADS, CT::BYTES);
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, THREADS, BYTES);
         if (err != cudaSuccess) return err;
         resident = sms * (per_sm > 0 ? per_sm : 1);
         if (dev < kDevices) resident_of[dev] = resident;
     }
-    const long long ncols =
-        (long long)((g.nx + SH::TX - 1) / SH::TX) * ((g.ny + SH::TY - 1) / SH::TY);
+    const long long ncols = (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
     int best_zc = g.nz;
     double best = -1.0;
     for (int nch = 1; nch <= g.nz && nch <= 64; ++nch) {
@@ -957,8 +959,7 @@ cudaError_t launch_column_ix(const Geo &g, const Ops<float> &T, const float *Qin
     const long long blocks = ncols * ((g.nz + best_zc - 1) / best_zc);
     if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
     ProfScope ps(prof, kKindStage, s);
-    column_stage_kernel<N, 0, MODE, Ix><<<(unsigned)blocks, CT::THREADS, CT::BYTES, s>>>(
-        Qin, Out, dQ, T, g, A, B, dt, best_zc);
+    kernel<<<(unsigned)blocks, THREADS, BYTES, s>>>(Qin, Out, dQ, T, g, A, B, dt, best_zc);
     return cudaGetLastError();
 }
 
@@ -969,9 +970,12 @@ cudaError_t launch_column(const Geo &g, const Ops<float> &T, const float *Qin, f
                           cudaStream_t s)
 {
     const long long floats = (long long)NF * g.E * N * N * N;
+    const bool lines = line_stage(N);
     if (floats <= 0x7fffffffLL)
-        return launch_column_ix<N, MODE, int>(g, T, Qin, Out, dQ, A, B, dt, prof, s);
-    return launch_column_ix<N, MODE, long long>(g, T, Qin, Out, dQ, A, B, dt, prof, s);
+        return lines ? launch_column_ix<N, MODE, int, true>(g, T, Qin, Out, dQ, A, B, dt, prof, s)
+                     : launch_column_ix<N, MODE, int, false>(g, T, Qin, Out, dQ, A, B, dt, prof, s);
+    return lines ? launch_column_ix<N, MODE, long long, true>(g, T, Qin, Out, dQ, A, B, dt, prof, s)
+                 : launch_column_ix<N, MODE, long long, false>(g, T, Qin, Out, dQ, A, B, dt, prof, s);
 }
 
 // The float form runs the single-pass column stage (DRAM bound: one read of

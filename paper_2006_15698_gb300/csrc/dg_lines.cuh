@@ -1,0 +1,299 @@
+// dg_lines.cuh -- the float form's single-mesh RK stage as a z-marching
+// column kernel with one thread per z node line.  Included by dg_kernels.cuh
+// (inside namespace dg), after dg_column.cuh, whose slot layout, prefetch,
+// traces and flux routines it shares.
+//
+// As in column_stage_kernel, a CTA walks a column of TX x TY elements up a
+// chunk of z layers and the layers ahead are staged in a ring of three
+// shared-memory slots by cp.async.  Here a thread owns the N nodes
+// (i, j, 0..N-1) of one element of the layer, so all work along z stays in
+// its registers: the z fluxes of its nodes and their weak z-derivative, the
+// traces at the two z ends of its line and the z interface flux above it
+// (kept as the next layer's -z face flux).  Per layer:
+//
+//   P  every thread: Euler fluxes (Eq. 2-3) of its nodes, x and y fluxes ->
+//      shared memory as x and y node lines; the z interface flux above its
+//      line (local Lax-Friedrichs, Sec. II.B) from its own +z trace and the
+//      -z trace of the line above in the next slot;
+//      interface tasks: the local Lax-Friedrichs flux at every x and y face
+//      point of the layer, each interface once, from the traces of the
+//      staged node lines on both sides (a neighbour column's line read
+//      through L2) -> shared memory
+//   G  every thread: weak derivative, lift of the six face fluxes and the
+//      stage update of its nodes -> DRAM
+//
+// Traces, interface fluxes, node fluxes, the derivative sums and the update
+// use the same functions in the same operation order as column_stage_kernel,
+// so the two kernels give the same floats.
+#pragma once
+
+// Column cross-sections per N (= p + 1): one thread per z line, 64 to 256
+// threads per CTA.
+template <int N, int V>
+struct LineShape;
+template <> struct LineShape<1, 0> { static constexpr int TX = 16, TY = 16; };
+template <> struct LineShape<2, 0> { static constexpr int TX = 8, TY = 8; };
+template <> struct LineShape<3, 0> { static constexpr int TX = 4, TY = 4; };
+template <> struct LineShape<4, 0> { static constexpr int TX = 2, TY = 2; };
+template <> struct LineShape<5, 0> { static constexpr int TX = 2, TY = 2; };
+template <> struct LineShape<6, 0> { static constexpr int TX = 2, TY = 1; };
+template <> struct LineShape<7, 0> { static constexpr int TX = 1, TY = 1; };
+
+template <int N, int TX, int TY>
+struct LineTile {
+    using CT = ColTile<N, TX, TY>;  // slot layout and prefetch units
+    static constexpr int N2 = N * N, N3 = N * N * N;
+    static constexpr int EPB = TX * TY;
+    static constexpr int THREADS = ((EPB * N2 + 31) / 32) * 32;
+    static constexpr int FSTR = CT::pad16(2 * NF * N3);  // fluxes [x, y][NF][N3] as node lines
+    static constexpr int HSTR = CT::HSTR;                // x, y face fluxes [2][NF][N2][(-,+)]
+    static constexpr size_t FLOATS =
+        (size_t)3 * CT::QSLOT + (size_t)EPB * (FSTR + HSTR) + CT::OPSF;
+    static constexpr size_t BYTES = FLOATS * sizeof(float);
+    static constexpr int XT = (TX + 1) * TY * N2, YT = (TY + 1) * TX * N2;
+};
+
+// trace of a staged node line (element el of the slot) at one end
+template <int N, int TX, int TY, int DIR>
+__device__ __forceinline__ void slot_trace(const float *slot, int el, int base, const float *l,
+                                           float q[NF])
+{
+    using CT = ColTile<N, TX, TY>;
+#pragma unroll
+    for (int n = 0; n < NF; ++n) {
+        float v[N];
+        line_values<N, DIR>(slot + (n * CT::EPB + el) * CT::ESTR + base, v);
+        q[n] = line_dot<N>(l, v);
+    }
+}
+
+// x (DIR 0) or y (DIR 1) interface a in [0, len] of row r at face point pt,
+// both traces from node lines (staged, or the neighbour column's in DRAM/L2)
+template <int N, int TX, int TY, int DIR, typename Ix>
+__device__ __forceinline__ void slot_interface(const float *__restrict__ Qin, const float *slot,
+                                               float *sH, const Geo &g, const float *lm,
+                                               const float *lp, float gamma, float gm1, int a,
+                                               int r, int len, Ix e_lo, Ix e_hi, int pt)
+{
+    using LT = LineTile<N, TX, TY>;
+    constexpr int N2 = LT::N2;
+    const int base = line_base<N, DIR>(pt % N, pt / N);
+    auto local = [&](int c) { return DIR == 0 ? r * TX + c : c * TX + r; };
+    float qL[NF], qR[NF];
+    if (a == 0) global_trace<N, DIR, Ix>(Qin, (Ix)g.E, e_lo, base, lp, qL);
+    else slot_trace<N, TX, TY, DIR>(slot, local(a - 1), base, lp, qL);
+    if (a == len) global_trace<N, DIR, Ix>(Qin, (Ix)g.E, e_hi, base, lm, qR);
+    else slot_trace<N, TX, TY, DIR>(slot, local(a), base, lm, qR);
+    float f[NF];
+    lf_flux2_f<DIR>(qL, qR, gamma, gm1, f);
+    if (a > 0) {
+        float *h = sH + (size_t)local(a - 1) * LT::HSTR + (DIR * NF * N2 + pt) * 2 + 1;
+#pragma unroll
+        for (int n = 0; n < NF; ++n) h[n * N2 * 2] = f[n];
+    }
+    if (a < len) {
+        float *h = sH + (size_t)local(a) * LT::HSTR + (DIR * NF * N2 + pt) * 2 + 0;
+#pragma unroll
+        for (int n = 0; n < NF; ++n) h[n * N2 * 2] = f[n];
+    }
+}
+
+// One column chunk of the stage; MODE and Ix as for column_stage_kernel.
+template <int N, int V, int MODE, typename Ix>
+__global__ void __launch_bounds__(LineTile<N, LineShape<N, V>::TX, LineShape<N, V>::TY>::THREADS)
+    line_stage_kernel(const float *__restrict__ Qin, float *__restrict__ Out,
+                      float *__restrict__ dQ, const Ops<float> T, const Geo g, float A, float B,
+                      const double *__restrict__ dt, int zchunk)
+{
+    constexpr int TX = LineShape<N, V>::TX, TY = LineShape<N, V>::TY;
+    using LT = LineTile<N, TX, TY>;
+    using CT = ColTile<N, TX, TY>;
+    constexpr int N2 = LT::N2, N3 = LT::N3, EPB = LT::EPB;
+    constexpr int FSTR = LT::FSTR, HSTR = LT::HSTR, ESTR = CT::ESTR;
+    extern __shared__ __align__(16) float lsm[];
+    float *slots = lsm;                            // [3][QSLOT]
+    float *sF = slots + 3 * CT::QSLOT;             // [EPB][FSTR]
+    float *sH = sF + EPB * FSTR;                   // [EPB][HSTR]
+    float *sOp = sH + EPB * HSTR;                  // D[3][N][N], Lm[3][N], Lp[3][N], lm[N], lp[N]
+
+    const int ncx = (g.nx + TX - 1) / TX, ncy = (g.ny + TY - 1) / TY;
+    const int col = (int)(blockIdx.x % (unsigned)(ncx * ncy));
+    const int chunk = (int)(blockIdx.x / (unsigned)(ncx * ncy));
+    const int ex0 = (col % ncx) * TX, ey0 = (col / ncx) * TY;
+    const int txv = min(TX, g.nx - ex0), tyv = min(TY, g.ny - ey0);
+    const int z0 = chunk * zchunk;
+    const int z1 = min(g.nz, z0 + zchunk);
+    const float dtr = MODE != 0 ? (float)(*dt) : 0.0f;
+    const float gamma = T.gamma, gm1 = T.gm1;
+
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int t = tid; t < 3 * N2 + 6 * N; t += nthr) {
+        float v;
+        if (t < 3 * N2) v = T.D[t / N2][(t % N2) / N][t % N];
+        else if (t < 3 * N2 + 3 * N) v = T.Lm[(t - 3 * N2) / N][(t - 3 * N2) % N];
+        else v = T.Lp[(t - 3 * N2 - 3 * N) / N][(t - 3 * N2 - 3 * N) % N];
+        sOp[t] = v;
+    }
+    for (int t = tid; t < 2 * N; t += nthr) sOp[3 * N2 + 6 * N + t] = t < N ? T.lm[t] : T.lp[t - N];
+    const float *lm = sOp + 3 * N2 + 6 * N, *lp = lm + N;
+
+    const int exL = (ex0 - 1 + g.nx) % g.nx, exR = (ex0 + txv) % g.nx;
+    const int eyL = (ey0 - 1 + g.ny) % g.ny, eyR = (ey0 + tyv) % g.ny;
+    const Ix plane = (Ix)g.nx * g.ny;
+    const Ix E = (Ix)g.E;
+
+    // this thread's z line (i, j) of element el
+    const int el = tid / N2;
+    const int ln = tid - el * N2;
+    const int a = el % TX, b = el / TX;
+    const bool active = el < EPB && a < txv && b < tyv;
+    const int i = ln % N, j = ln / N;
+
+    auto slot_of = [&](int L) { return slots + ((L - z0 + 1) % 3) * CT::QSLOT; };
+    auto zmod = [&](int L) { return (L % g.nz + g.nz) % g.nz; };
+    // node line (i, j) of this thread's element in a slot, per field
+    auto load_zline = [&](const float *slot, float v[NF][N]) {
+#pragma unroll
+        for (int n = 0; n < NF; ++n)
+#pragma unroll
+            for (int c = 0; c < N; ++c) v[n][c] = slot[(n * EPB + el) * ESTR + (c * N + j) * N + i];
+    };
+
+    column_prefetch<N, TX, TY, Ix>(Qin, slot_of(z0 - 1), g, ex0, ey0, txv, tyv, zmod(z0 - 1));
+    column_prefetch<N, TX, TY, Ix>(Qin, slot_of(z0), g, ex0, ey0, txv, tyv, zmod(z0));
+    column_prefetch<N, TX, TY, Ix>(Qin, slot_of(z0 + 1), g, ex0, ey0, txv, tyv, zmod(z0 + 1));
+    cp_async_wait_all();
+    __syncthreads();
+
+    // operator values of this thread's line, for the whole chunk
+    float lmr[N], lpr[N], dx[N], dy[N];
+    load_line<N>(lm, lmr);
+    load_line<N>(lp, lpr);
+    load_line<N>(sOp + 0 * N2 + i * N, dx);
+    load_line<N>(sOp + 1 * N2 + j * N, dy);
+    const float *Lm = sOp + 3 * N2, *Lp = Lm + 3 * N;
+    const float lmx = Lm[i], lmy = Lm[N + j], lpx = Lp[i], lpy = Lp[N + j];
+
+    // flux through the -z face of the line in the current layer
+    float fzm[NF];
+    if (active) {
+        float v[NF][N], tp[NF], tm[NF];
+        load_zline(slot_of(z0 - 1), v);
+#pragma unroll
+        for (int n = 0; n < NF; ++n) tp[n] = line_dot<N>(lpr, v[n]);
+        load_zline(slot_of(z0), v);
+#pragma unroll
+        for (int n = 0; n < NF; ++n) tm[n] = line_dot<N>(lmr, v[n]);
+        lf_flux2_f<2>(tp, tm, gamma, gm1, fzm);
+    }
+    __syncthreads();
+    if (z0 + 2 <= z1)
+        column_prefetch<N, TX, TY, Ix>(Qin, slot_of(z0 + 2), g, ex0, ey0, txv, tyv, zmod(z0 + 2));
+
+    for (int z = z0; z < z1; ++z) {
+        const float *cur = slot_of(z), *nxt = slot_of(z + 1);
+        const Ix e = ex0 + a + (Ix)g.nx * (ey0 + b) + plane * z;
+
+        // P: node fluxes, the z interface above the line, x and y interfaces
+        float qc[NF][N], fz[NF][N], fzp[NF], dq[NF][N];
+        if (active) {
+            if (MODE != 0 && A != 0.0f) {
+#pragma unroll
+                for (int n = 0; n < NF; ++n)
+#pragma unroll
+                    for (int c = 0; c < N; ++c)
+                        dq[n][c] = dQ[((Ix)n * E + e) * N3 + (c * N + j) * N + i];
+            }
+            load_zline(cur, qc);
+            float *sx = sF + (size_t)el * FSTR;
+            float *sy = sx + NF * N3;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                float q[NF], fx[NF], fy[NF], f3[NF];
+#pragma unroll
+                for (int n = 0; n < NF; ++n) q[n] = qc[n][c];
+                node_flux_f(q, gm1, fx, fy, f3);
+#pragma unroll
+                for (int n = 0; n < NF; ++n) {
+                    sx[n * N3 + (c * N + j) * N + i] = fx[n];
+                    sy[n * N3 + (c * N + i) * N + j] = fy[n];
+                    fz[n][c] = f3[n];
+                }
+            }
+            float v[NF][N], tp[NF], tm[NF];
+            load_zline(nxt, v);
+#pragma unroll
+            for (int n = 0; n < NF; ++n) {
+                tp[n] = line_dot<N>(lpr, qc[n]);
+                tm[n] = line_dot<N>(lmr, v[n]);
+            }
+            lf_flux2_f<2>(tp, tm, gamma, gm1, fzp);
+        }
+        for (int t = tid; t < LT::XT + LT::YT; t += nthr) {
+            if (t < LT::XT) {
+                // interface index slowest, so that a warp shares its source
+                const int ai = t / (TY * N2), r = t - ai * (TY * N2);
+                const int row = r / N2, pt = r - row * N2;
+                if (ai > txv || row >= tyv) continue;
+                const Ix er = (Ix)g.nx * (ey0 + row) + plane * z;
+                slot_interface<N, TX, TY, 0, Ix>(Qin, cur, sH, g, lm, lp, gamma, gm1, ai, row,
+                                                 txv, exL + er, exR + er, pt);
+            } else {
+                const int u = t - LT::XT;
+                const int ai = u / (TX * N2), r = u - ai * (TX * N2);
+                const int cx = r / N2, pt = r - cx * N2;
+                if (ai > tyv || cx >= txv) continue;
+                const Ix ec = ex0 + cx + plane * z;
+                slot_interface<N, TX, TY, 1, Ix>(Qin, cur, sH, g, lm, lp, gamma, gm1, ai, cx,
+                                                 tyv, ec + (Ix)g.nx * eyL, ec + (Ix)g.nx * eyR, pt);
+            }
+        }
+        __syncthreads();
+
+        // G: derivative, lift, update of the line's nodes
+        if (active) {
+            const float *h = sH + (size_t)el * HSTR;
+            const float *fxl = sF + (size_t)el * FSTR;
+            const float *fyl = fxl + NF * N3;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                float dz[N];
+                load_line<N>(sOp + 2 * N2 + c * N, dz);
+                const float lmz = Lm[2 * N + c], lpz = Lp[2 * N + c];
+                const int node = (c * N + j) * N + i, px = c * N + j, py = c * N + i;
+#pragma unroll
+                for (int n = 0; n < NF; ++n) {
+                    float vx[N], vy[N];
+                    load_line<N>(fxl + n * N3 + px * N, vx);
+                    load_line<N>(fyl + n * N3 + py * N, vy);
+                    float2 a2 = f2(0.0f, 0.0f);
+                    a2 = dot2_acc<N>(dx, vx, a2);
+                    a2 = dot2_acc<N>(dy, vy, a2);
+                    a2 = dot2_acc<N>(dz, fz[n], a2);
+                    const float2 hx = *reinterpret_cast<const float2 *>(h + ((0 * NF + n) * N2 + px) * 2);
+                    const float2 hy = *reinterpret_cast<const float2 *>(h + ((1 * NF + n) * N2 + py) * 2);
+                    a2 = __ffma2_rn(f2(lmx, -lpx), hx, a2);
+                    a2 = __ffma2_rn(f2(lmy, -lpy), hy, a2);
+                    a2 = __ffma2_rn(f2(lmz, -lpz), f2(fzm[n], fzp[n]), a2);
+                    const float acc = __fadd_rn(a2.x, a2.y);
+                    const Ix o = ((Ix)n * E + e) * N3 + node;
+                    if (MODE == 0) {
+                        Out[o] = acc;
+                    } else {
+                        const float d = __fmaf_rn(dtr, acc, A == 0.0f ? 0.0f : __fmul_rn(A, dq[n][c]));
+                        dQ[o] = d;
+                        if (MODE == 1) Out[o] = __fmaf_rn(B, d, qc[n][c]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int n = 0; n < NF; ++n) fzm[n] = fzp[n];
+        }
+        // the slot of layer z is free once every thread is past G
+        cp_async_wait_all();
+        __syncthreads();
+        if (z + 3 <= z1)
+            column_prefetch<N, TX, TY, Ix>(Qin, slots + ((z - z0 + 1) % 3) * CT::QSLOT, g, ex0,
+                                           ey0, txv, tyv, zmod(z + 3));
+    }
+}

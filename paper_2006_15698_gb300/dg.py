@@ -316,7 +316,8 @@ def dg_get_tile_variant(p):
     return _lib.dg_get_tile_variant(p)
 
 
-DG_STAGE_TILE, DG_STAGE_COLUMN = 0, 1
+DG_STAGE_TILE, DG_STAGE_COLUMN, DG_STAGE_LINES = 0, 1, 2
+STAGE_KINDS = {"tile": DG_STAGE_TILE, "column": DG_STAGE_COLUMN, "lines": DG_STAGE_LINES}
 
 
 def dg_set_stage_kernel(p, kind):
@@ -333,8 +334,8 @@ TUNING_PATH = os.path.join(_HERE, "tuning", "fused_tiles.json")
 def load_tuning(path=None):
     """Select the tile variant and the single-mesh stage kernel per degree
     from an autotuner table (JSON with "variant" and optionally "kernel"
-    ("tile" or "column") entries per degree); returns the table, or None if
-    absent."""
+    ("tile", "column" or "lines") entries per degree); returns the table, or
+    None if absent."""
     import json
     path = path or TUNING_PATH
     if not os.path.exists(path):
@@ -346,8 +347,8 @@ def load_tuning(path=None):
         if 0 <= v < dg_tile_variant_count(int(p)):
             dg_set_tile_variant(int(p), v)
         kind = ent.get("kernel")
-        if kind in ("tile", "column"):
-            dg_set_stage_kernel(int(p), DG_STAGE_COLUMN if kind == "column" else DG_STAGE_TILE)
+        if kind in STAGE_KINDS:
+            dg_set_stage_kernel(int(p), STAGE_KINDS[kind])
     return table
 
 

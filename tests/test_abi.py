@@ -84,7 +84,7 @@ def test_tuning_tables_validate_on_host(lib):
     lib.dg_get_tile_variant.argtypes = [ctypes.c_int]
     lib.dg_tile_variant_count.argtypes = [ctypes.c_int]
     for p in range(7):
-        assert lib.dg_get_stage_kernel(p) in (0, 1)
+        assert lib.dg_get_stage_kernel(p) in (0, 1, 2)
         assert lib.dg_tile_variant_count(p) >= 1
     assert lib.dg_get_stage_kernel(-1) == -1 and lib.dg_get_stage_kernel(7) == -1
     assert lib.dg_set_stage_kernel(7, 0) == 2          # DG_ERR_UNSUPPORTED
@@ -92,5 +92,7 @@ def test_tuning_tables_validate_on_host(lib):
     saved = lib.dg_get_stage_kernel(3)
     assert lib.dg_set_stage_kernel(3, 0) == 0 and lib.dg_get_stage_kernel(3) == 0
     assert lib.dg_set_stage_kernel(3, 1) == 0 and lib.dg_get_stage_kernel(3) == 1
+    assert lib.dg_set_stage_kernel(3, 2) == 0 and lib.dg_get_stage_kernel(3) == 2
+    assert lib.dg_set_stage_kernel(3, 3) == 1
     lib.dg_set_stage_kernel(3, saved)
     assert lib.dg_set_tile_variant(3, lib.dg_tile_variant_count(3)) == 1

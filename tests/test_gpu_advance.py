@@ -36,7 +36,8 @@ def _separate(m, Q, dQ, cfl, n):
 CASES = [("fp64", 2, (5, 3, 2), None), ("fp64", 4, (3, 3, 3), None), ("fp64", 0, (4, 1, 3), None),
          ("fp32", 3, (5, 7, 6), "column"), ("fp32", 3, (5, 7, 6), "tile"),
          ("fp32", 1, (4, 3, 5), "tile"), ("fp32", 5, (2, 3, 4), "column"),
-         ("fp32", 6, (1, 2, 3), "tile")]
+         ("fp32", 6, (1, 2, 3), "tile"), ("fp32", 3, (5, 7, 6), "lines"),
+         ("fp32", 2, (9, 4, 3), "lines"), ("fp32", 6, (3, 1, 4), "lines")]
 
 
 @pytest.mark.parametrize("prec,p,nel,kernel", CASES)
@@ -48,7 +49,7 @@ def test_advance_equals_separate_calls(prec, p, nel, kernel):
     saved = dg.dg_get_stage_kernel(p)
     try:
         if kernel:
-            dg.dg_set_stage_kernel(p, dg.DG_STAGE_COLUMN if kernel == "column" else dg.DG_STAGE_TILE)
+            dg.dg_set_stage_kernel(p, dg.STAGE_KINDS[kernel])
         om = oracle.Mesh(*nel, p, *BOX)
         Q0 = to_dev(_state(om, 5 + p), dtype)
         m = dg.Mesh(*nel, p, *BOX, precision=fp)

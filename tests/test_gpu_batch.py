@@ -164,7 +164,7 @@ def test_batch_rejects_bad_specs(dgm):
         dg.Batch([dict(nx=0, ny=2, nz=2, p=1)])
 
 
-@pytest.mark.parametrize("kernel", ["column", "tile"])
+@pytest.mark.parametrize("kernel", ["column", "lines", "tile"])
 def test_hybrid_batch_large_instances_match_single_meshes(dgm, kernel):
     """Instances of at least 2^19 nodes run the single-mesh stage kernels as
     launches of their own inside the batch's step (and graph); each still
@@ -176,8 +176,8 @@ def test_hybrid_batch_large_instances_match_single_meshes(dgm, kernel):
     # instances (degrees 2, 5) share the batched tile launch, so their single
     # meshes use the tile kernel too
     for p in range(0, 7):
-        big = p in (3, 4) and kernel == "column"
-        dg.dg_set_stage_kernel(p, dg.DG_STAGE_COLUMN if big else dg.DG_STAGE_TILE)
+        big = p in (3, 4)
+        dg.dg_set_stage_kernel(p, dg.STAGE_KINDS[kernel] if big else dg.DG_STAGE_TILE)
     specs = [dict(nx=24, ny=24, nz=24, p=3, Lx=10.0, Ly=10.0, Lz=10.0),   # 884,736 nodes: own launches
              dict(nx=5, ny=6, nz=5, p=2, Lx=10.0, Ly=10.0, Lz=10.0),
              dict(nx=12, ny=10, nz=9, p=5, Lx=10.0, Ly=10.0, Lz=10.0),    # 233,280 nodes: shared
