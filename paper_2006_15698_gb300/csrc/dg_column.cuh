@@ -206,8 +206,25 @@ __device__ __forceinline__ void node_flux_f(const float q[NF], float gm1, float 
     fz[4] = __fmul_rn(ep, w);
 }
 
+// Position in a slot of the node at offset o = (k N + j) N + i of its
+// element.  SWZ (N = 4 only): the 16-byte x-line (j, k) is stored at line
+// 4 k + (j xor r(k)), r(k) the bit reversal of k, so that both the z lines
+// (fixed i, j) and the y lines (fixed i, k) of two neighbouring elements
+// read by one warp fall into 32 distinct banks.
+template <int N, bool SWZ>
+__device__ __forceinline__ int slot_pos(int o)
+{
+    if constexpr (SWZ) {
+        static_assert(N == 4, "the slot swizzle is defined for N = 4");
+        const int k = o >> 4, j = (o >> 2) & 3;
+        return ((k << 2) | (j ^ (((k & 1) << 1) | (k >> 1)))) * 4 + (o & 3);
+    } else {
+        return o;
+    }
+}
+
 // Copy layer zl (periodic) of the column into a slot: whole valid rows.
-template <int N, int TX, int TY, typename Ix>
+template <int N, int TX, int TY, typename Ix, bool SWZ = false>
 __device__ __forceinline__ void column_prefetch(const float *__restrict__ Q, float *slot,
                                                 const Geo &g, int ex0, int ey0, int txv, int tyv,
                                                 int zl)
@@ -224,7 +241,7 @@ __device__ __forceinline__ void column_prefetch(const float *__restrict__ Q, flo
         const Ix e0 = ex0 + (Ix)g.nx * (ey0 + b) + plane * zl;
         const float *src = Q + ((Ix)n * (Ix)g.E + e0) * N3 + u * W;
         const int a = (u * W) / N3, o = u * W - a * N3;  // element of the row, node offset
-        float *dst = slot + (n * EPB + b * TX + a) * CT::ESTR + o;
+        float *dst = slot + (n * EPB + b * TX + a) * CT::ESTR + slot_pos<N, SWZ>(o);
         if constexpr (W == 4) cp_async16(dst, src);
         else cp_async4(dst, src);
     }

@@ -922,8 +922,9 @@ cudaError_t launch_column_ix(const Geo &g, const Ops<float> &T, const float *Qin
 {
     constexpr int TX = LINES ? LineShape<N, 0>::TX : ColShape<N, 0>::TX;
     constexpr int TY = LINES ? LineShape<N, 0>::TY : ColShape<N, 0>::TY;
-    constexpr int THREADS = LINES ? LineTile<N, TX, TY>::THREADS : ColTile<N, TX, TY>::THREADS;
-    constexpr size_t BYTES = LINES ? LineTile<N, TX, TY>::BYTES : ColTile<N, TX, TY>::BYTES;
+    using LT = LineTile<N, TX, TY, LineShape<N, 0>::DB, LineShape<N, 0>::NS>;
+    constexpr int THREADS = LINES ? LT::THREADS : ColTile<N, TX, TY>::THREADS;
+    constexpr size_t BYTES = LINES ? LT::BYTES : ColTile<N, TX, TY>::BYTES;
     auto kernel = LINES ? line_stage_kernel<N, 0, MODE, Ix> : column_stage_kernel<N, 0, MODE, Ix>;
     // CTAs of this kernel resident on a device at once, per device (a benign
     // race: concurrent first calls store the same value)

@@ -4,8 +4,8 @@
 // traces and flux routines it shares.
 //
 // As in column_stage_kernel, a CTA walks a column of TX x TY elements up a
-// chunk of z layers and the layers ahead are staged in a ring of three
-// shared-memory slots by cp.async.  Here a thread owns the N nodes
+// chunk of z layers and the layers ahead are staged in a ring of shared-
+// memory slots by cp.async.  Here a thread owns the N nodes
 // (i, j, 0..N-1) of one element of the layer, so all work along z stays in
 // its registers: the z fluxes of its nodes and their weak z-derivative, the
 // traces at the two z ends of its line and the z interface flux above it
@@ -28,18 +28,30 @@
 #pragma once
 
 // Column cross-sections per N (= p + 1): one thread per z line, 64 to 256
-// threads per CTA.
+// threads per CTA.  DB: fluxes and face fluxes double-buffered by layer
+// parity, so one barrier per layer separates the two phases instead of two.
+// NS: slots in the ring of staged layers (3: the layer two ahead is fetched
+// during a whole layer; 2: during the second phase only, less shared
+// memory).  MINB: CTAs per SM the registers are sized for (0: the compiler's
+// choice).  SWZ: swizzled slot layout (slot_pos).
 template <int N, int V>
 struct LineShape;
-template <> struct LineShape<1, 0> { static constexpr int TX = 16, TY = 16; };
-template <> struct LineShape<2, 0> { static constexpr int TX = 8, TY = 8; };
-template <> struct LineShape<3, 0> { static constexpr int TX = 4, TY = 4; };
-template <> struct LineShape<4, 0> { static constexpr int TX = 2, TY = 2; };
-template <> struct LineShape<5, 0> { static constexpr int TX = 2, TY = 2; };
-template <> struct LineShape<6, 0> { static constexpr int TX = 2, TY = 1; };
-template <> struct LineShape<7, 0> { static constexpr int TX = 1, TY = 1; };
+struct LineDefaults {
+    static constexpr bool DB = false, SWZ = false;
+    static constexpr int NS = 3, MINB = 0;
+};
+template <> struct LineShape<1, 0> : LineDefaults { static constexpr int TX = 16, TY = 16, NS = 2; };
+template <> struct LineShape<2, 0> : LineDefaults { static constexpr int TX = 8, TY = 8, NS = 2; };
+template <> struct LineShape<3, 0> : LineDefaults { static constexpr int TX = 4, TY = 4, NS = 2; };
+template <> struct LineShape<4, 0> : LineDefaults {
+    static constexpr int TX = 2, TY = 2, NS = 2;
+    static constexpr bool SWZ = true;
+};
+template <> struct LineShape<5, 0> : LineDefaults { static constexpr int TX = 2, TY = 2, NS = 2; };
+template <> struct LineShape<6, 0> : LineDefaults { static constexpr int TX = 2, TY = 1; };
+template <> struct LineShape<7, 0> : LineDefaults { static constexpr int TX = 1, TY = 1; };
 
-template <int N, int TX, int TY>
+template <int N, int TX, int TY, bool DB = false, int NS = 3>
 struct LineTile {
     using CT = ColTile<N, TX, TY>;  // slot layout and prefetch units
     static constexpr int N2 = N * N, N3 = N * N * N;
@@ -47,29 +59,38 @@ struct LineTile {
     static constexpr int THREADS = ((EPB * N2 + 31) / 32) * 32;
     static constexpr int FSTR = CT::pad16(2 * NF * N3);  // fluxes [x, y][NF][N3] as node lines
     static constexpr int HSTR = CT::HSTR;                // x, y face fluxes [2][NF][N2][(-,+)]
+    static constexpr int NBUF = DB ? 2 : 1;
     static constexpr size_t FLOATS =
-        (size_t)3 * CT::QSLOT + (size_t)EPB * (FSTR + HSTR) + CT::OPSF;
+        (size_t)NS * CT::QSLOT + (size_t)NBUF * EPB * (FSTR + HSTR) + CT::OPSF;
     static constexpr size_t BYTES = FLOATS * sizeof(float);
     static constexpr int XT = (TX + 1) * TY * N2, YT = (TY + 1) * TX * N2;
 };
 
-// trace of a staged node line (element el of the slot) at one end
-template <int N, int TX, int TY, int DIR>
+// trace of a staged node line (element el of the slot) at one end; base is
+// the line's first node (line_base)
+template <int N, int TX, int TY, int DIR, bool SWZ>
 __device__ __forceinline__ void slot_trace(const float *slot, int el, int base, const float *l,
                                            float q[NF])
 {
     using CT = ColTile<N, TX, TY>;
+    constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? N : N * N);
 #pragma unroll
     for (int n = 0; n < NF; ++n) {
+        const float *e = slot + (n * CT::EPB + el) * CT::ESTR;
         float v[N];
-        line_values<N, DIR>(slot + (n * CT::EPB + el) * CT::ESTR + base, v);
+        if constexpr (DIR == 0) {
+            load_line<N>(e + slot_pos<N, SWZ>(base), v);   // an x line is one 16-byte unit
+        } else {
+#pragma unroll
+            for (int c = 0; c < N; ++c) v[c] = e[slot_pos<N, SWZ>(base + c * stride)];
+        }
         q[n] = line_dot<N>(l, v);
     }
 }
 
 // x (DIR 0) or y (DIR 1) interface a in [0, len] of row r at face point pt,
 // both traces from node lines (staged, or the neighbour column's in DRAM/L2)
-template <int N, int TX, int TY, int DIR, typename Ix>
+template <int N, int TX, int TY, int DIR, typename Ix, bool SWZ>
 __device__ __forceinline__ void slot_interface(const float *__restrict__ Qin, const float *slot,
                                                float *sH, const Geo &g, const float *lm,
                                                const float *lp, float gamma, float gm1, int a,
@@ -81,9 +102,9 @@ __device__ __forceinline__ void slot_interface(const float *__restrict__ Qin, co
     auto local = [&](int c) { return DIR == 0 ? r * TX + c : c * TX + r; };
     float qL[NF], qR[NF];
     if (a == 0) global_trace<N, DIR, Ix>(Qin, (Ix)g.E, e_lo, base, lp, qL);
-    else slot_trace<N, TX, TY, DIR>(slot, local(a - 1), base, lp, qL);
+    else slot_trace<N, TX, TY, DIR, SWZ>(slot, local(a - 1), base, lp, qL);
     if (a == len) global_trace<N, DIR, Ix>(Qin, (Ix)g.E, e_hi, base, lm, qR);
-    else slot_trace<N, TX, TY, DIR>(slot, local(a), base, lm, qR);
+    else slot_trace<N, TX, TY, DIR, SWZ>(slot, local(a), base, lm, qR);
     float f[NF];
     lf_flux2_f<DIR>(qL, qR, gamma, gm1, f);
     if (a > 0) {
@@ -100,21 +121,26 @@ __device__ __forceinline__ void slot_interface(const float *__restrict__ Qin, co
 
 // One column chunk of the stage; MODE and Ix as for column_stage_kernel.
 template <int N, int V, int MODE, typename Ix>
-__global__ void __launch_bounds__(LineTile<N, LineShape<N, V>::TX, LineShape<N, V>::TY>::THREADS)
+__global__ void __launch_bounds__(
+    LineTile<N, LineShape<N, V>::TX, LineShape<N, V>::TY, LineShape<N, V>::DB>::THREADS,
+    LineShape<N, V>::MINB)
     line_stage_kernel(const float *__restrict__ Qin, float *__restrict__ Out,
                       float *__restrict__ dQ, const Ops<float> T, const Geo g, float A, float B,
                       const double *__restrict__ dt, int zchunk)
 {
     constexpr int TX = LineShape<N, V>::TX, TY = LineShape<N, V>::TY;
-    using LT = LineTile<N, TX, TY>;
+    constexpr bool DB = LineShape<N, V>::DB, SWZ = LineShape<N, V>::SWZ;
+    constexpr int NS = LineShape<N, V>::NS;
+    static_assert(NS == 3 || (NS == 2 && !DB), "two slots need the two-barrier layer");
+    using LT = LineTile<N, TX, TY, DB, NS>;
     using CT = ColTile<N, TX, TY>;
     constexpr int N2 = LT::N2, N3 = LT::N3, EPB = LT::EPB;
     constexpr int FSTR = LT::FSTR, HSTR = LT::HSTR, ESTR = CT::ESTR;
     extern __shared__ __align__(16) float lsm[];
-    float *slots = lsm;                            // [3][QSLOT]
-    float *sF = slots + 3 * CT::QSLOT;             // [EPB][FSTR]
-    float *sH = sF + EPB * FSTR;                   // [EPB][HSTR]
-    float *sOp = sH + EPB * HSTR;                  // D[3][N][N], Lm[3][N], Lp[3][N], lm[N], lp[N]
+    float *slots = lsm;                            // [NS][QSLOT]
+    float *sF0 = slots + NS * CT::QSLOT;           // [NBUF][EPB][FSTR]
+    float *sH0 = sF0 + LT::NBUF * EPB * FSTR;      // [NBUF][EPB][HSTR]
+    float *sOp = sH0 + LT::NBUF * EPB * HSTR;      // D[3][N][N], Lm[3][N], Lp[3][N], lm[N], lp[N]
 
     const int ncx = (g.nx + TX - 1) / TX, ncy = (g.ny + TY - 1) / TY;
     const int col = (int)(blockIdx.x % (unsigned)(ncx * ncy));
@@ -149,19 +175,23 @@ __global__ void __launch_bounds__(LineTile<N, LineShape<N, V>::TX, LineShape<N, 
     const bool active = el < EPB && a < txv && b < tyv;
     const int i = ln % N, j = ln / N;
 
-    auto slot_of = [&](int L) { return slots + ((L - z0 + 1) % 3) * CT::QSLOT; };
+    auto slot_of = [&](int L) { return slots + ((L - z0 + 1) % NS) * CT::QSLOT; };
     auto zmod = [&](int L) { return (L % g.nz + g.nz) % g.nz; };
     // node line (i, j) of this thread's element in a slot, per field
     auto load_zline = [&](const float *slot, float v[NF][N]) {
 #pragma unroll
         for (int n = 0; n < NF; ++n)
 #pragma unroll
-            for (int c = 0; c < N; ++c) v[n][c] = slot[(n * EPB + el) * ESTR + (c * N + j) * N + i];
+            for (int c = 0; c < N; ++c)
+                v[n][c] = slot[(n * EPB + el) * ESTR + slot_pos<N, SWZ>((c * N + j) * N + i)];
+    };
+    auto prefetch = [&](int L) {
+        column_prefetch<N, TX, TY, Ix, SWZ>(Qin, slot_of(L), g, ex0, ey0, txv, tyv, zmod(L));
     };
 
-    column_prefetch<N, TX, TY, Ix>(Qin, slot_of(z0 - 1), g, ex0, ey0, txv, tyv, zmod(z0 - 1));
-    column_prefetch<N, TX, TY, Ix>(Qin, slot_of(z0), g, ex0, ey0, txv, tyv, zmod(z0));
-    column_prefetch<N, TX, TY, Ix>(Qin, slot_of(z0 + 1), g, ex0, ey0, txv, tyv, zmod(z0 + 1));
+    prefetch(z0 - 1);
+    prefetch(z0);
+    if constexpr (NS == 3) prefetch(z0 + 1);
     cp_async_wait_all();
     __syncthreads();
 
@@ -187,12 +217,19 @@ __global__ void __launch_bounds__(LineTile<N, LineShape<N, V>::TX, LineShape<N, 
         lf_flux2_f<2>(tp, tm, gamma, gm1, fzm);
     }
     __syncthreads();
-    if (z0 + 2 <= z1)
-        column_prefetch<N, TX, TY, Ix>(Qin, slot_of(z0 + 2), g, ex0, ey0, txv, tyv, zmod(z0 + 2));
+    if constexpr (NS == 3) {
+        if (z0 + 2 <= z1) prefetch(z0 + 2);
+    } else {
+        prefetch(z0 + 1);   // into the slot of z0 - 1, free now
+        cp_async_wait_all();
+        __syncthreads();
+    }
 
     for (int z = z0; z < z1; ++z) {
         const float *cur = slot_of(z), *nxt = slot_of(z + 1);
         const Ix e = ex0 + a + (Ix)g.nx * (ey0 + b) + plane * z;
+        float *sF = sF0 + (DB ? (z & 1) * EPB * FSTR : 0);
+        float *sH = sH0 + (DB ? (z & 1) * EPB * HSTR : 0);
 
         // P: node fluxes, the z interface above the line, x and y interfaces
         float qc[NF][N], fz[NF][N], fzp[NF], dq[NF][N];
@@ -236,7 +273,7 @@ __global__ void __launch_bounds__(LineTile<N, LineShape<N, V>::TX, LineShape<N, 
                 const int row = r / N2, pt = r - row * N2;
                 if (ai > txv || row >= tyv) continue;
                 const Ix er = (Ix)g.nx * (ey0 + row) + plane * z;
-                slot_interface<N, TX, TY, 0, Ix>(Qin, cur, sH, g, lm, lp, gamma, gm1, ai, row,
+                slot_interface<N, TX, TY, 0, Ix, SWZ>(Qin, cur, sH, g, lm, lp, gamma, gm1, ai, row,
                                                  txv, exL + er, exR + er, pt);
             } else {
                 const int u = t - LT::XT;
@@ -244,11 +281,22 @@ __global__ void __launch_bounds__(LineTile<N, LineShape<N, V>::TX, LineShape<N, 
                 const int cx = r / N2, pt = r - cx * N2;
                 if (ai > tyv || cx >= txv) continue;
                 const Ix ec = ex0 + cx + plane * z;
-                slot_interface<N, TX, TY, 1, Ix>(Qin, cur, sH, g, lm, lp, gamma, gm1, ai, cx,
+                slot_interface<N, TX, TY, 1, Ix, SWZ>(Qin, cur, sH, g, lm, lp, gamma, gm1, ai, cx,
                                                  tyv, ec + (Ix)g.nx * eyL, ec + (Ix)g.nx * eyR, pt);
             }
         }
-        __syncthreads();
+        if constexpr (DB) {
+            // every thread is past P: the slot of layer z is free, and the
+            // layer z + 2 copies are complete and visible after the barrier
+            cp_async_wait_all();
+            __syncthreads();
+            if (z + 3 <= z1) prefetch(z + 3);
+        } else {
+            __syncthreads();
+            // two slots: the slot of layer z is free once every thread is past P
+            if constexpr (NS == 2)
+                if (z + 2 <= z1) prefetch(z + 2);
+        }
 
         // G: derivative, lift, update of the line's nodes
         if (active) {
@@ -289,11 +337,13 @@ __global__ void __launch_bounds__(LineTile<N, LineShape<N, V>::TX, LineShape<N, 
 #pragma unroll
             for (int n = 0; n < NF; ++n) fzm[n] = fzp[n];
         }
-        // the slot of layer z is free once every thread is past G
-        cp_async_wait_all();
-        __syncthreads();
-        if (z + 3 <= z1)
-            column_prefetch<N, TX, TY, Ix>(Qin, slots + ((z - z0 + 1) % 3) * CT::QSLOT, g, ex0,
-                                           ey0, txv, tyv, zmod(z + 3));
+        if constexpr (!DB) {
+            // the fluxes, face fluxes and the slot of layer z are free once
+            // every thread is past G
+            cp_async_wait_all();
+            __syncthreads();
+            if constexpr (NS == 3)
+                if (z + 3 <= z1) prefetch(z + 3);
+        }
     }
 }
