@@ -33,11 +33,12 @@
 // NS: slots in the ring of staged layers (3: the layer two ahead is fetched
 // during a whole layer; 2: during the second phase only, less shared
 // memory).  MINB: CTAs per SM the registers are sized for (0: the compiler's
-// choice).  SWZ: swizzled slot layout (slot_pos).
+// choice).  SWZ: swizzled slot layout (slot_pos).  UT: the interface-task
+// loop unrolled (more independent work per thread, more registers).
 template <int N, int V>
 struct LineShape;
 struct LineDefaults {
-    static constexpr bool DB = false, SWZ = false;
+    static constexpr bool DB = false, SWZ = false, UT = false;
     static constexpr int NS = 3, MINB = 0;
 };
 template <> struct LineShape<1, 0> : LineDefaults { static constexpr int TX = 16, TY = 16, NS = 2; };
@@ -45,10 +46,13 @@ template <> struct LineShape<2, 0> : LineDefaults { static constexpr int TX = 8,
 template <> struct LineShape<3, 0> : LineDefaults { static constexpr int TX = 4, TY = 4, NS = 2; };
 template <> struct LineShape<4, 0> : LineDefaults {
     static constexpr int TX = 2, TY = 2, NS = 2;
-    static constexpr bool SWZ = true;
+    static constexpr bool SWZ = true, UT = true;
 };
 template <> struct LineShape<5, 0> : LineDefaults { static constexpr int TX = 2, TY = 2, NS = 2; };
-template <> struct LineShape<6, 0> : LineDefaults { static constexpr int TX = 2, TY = 1; };
+template <> struct LineShape<6, 0> : LineDefaults {
+    static constexpr int TX = 2, TY = 1;
+    static constexpr bool UT = true;
+};
 template <> struct LineShape<7, 0> : LineDefaults { static constexpr int TX = 1, TY = 1; };
 
 template <int N, int TX, int TY, bool DB = false, int NS = 3>
@@ -185,8 +189,43 @@ __global__ void __launch_bounds__(
             for (int c = 0; c < N; ++c)
                 v[n][c] = slot[(n * EPB + el) * ESTR + slot_pos<N, SWZ>((c * N + j) * N + i)];
     };
+    // This thread's share of a layer's copy: the same units every layer, so
+    // their offsets (source relative to the layer, destination relative to
+    // the slot) are computed once (W = 4: 16-byte units; else per layer).
+    constexpr int W = CT::W, RU = CT::ROW_UNITS;
+    constexpr int UNITS = NF * TY * RU;
+    constexpr int MAXC = (UNITS + LT::THREADS - 1) / LT::THREADS;
+    constexpr bool PRE = W == 4 && MAXC <= 6;
+    Ix csrc[PRE ? MAXC : 1];
+    int cdst[PRE ? MAXC : 1];
+    if constexpr (PRE) {
+#pragma unroll
+        for (int m = 0; m < MAXC; ++m) {
+            const int t = tid + m * LT::THREADS;
+            const int n = t / (TY * RU);
+            const int r = t - n * (TY * RU);
+            const int bb = r / RU;
+            const int u = r - bb * RU;
+            cdst[m] = -1;
+            csrc[m] = 0;
+            if (t < UNITS && bb < tyv && u * W < txv * N3) {
+                const int ea = (u * W) / N3, o = u * W - ea * N3;
+                csrc[m] = ((Ix)n * E + ex0 + (Ix)g.nx * (ey0 + bb)) * N3 + u * W;
+                cdst[m] = (n * EPB + bb * TX + ea) * ESTR + slot_pos<N, SWZ>(o);
+            }
+        }
+    }
     auto prefetch = [&](int L) {
-        column_prefetch<N, TX, TY, Ix, SWZ>(Qin, slot_of(L), g, ex0, ey0, txv, tyv, zmod(L));
+        if constexpr (PRE) {
+            const float *src = Qin + plane * (Ix)zmod(L) * N3;
+            float *dst = slot_of(L);
+#pragma unroll
+            for (int m = 0; m < MAXC; ++m)
+                if (cdst[m] >= 0) cp_async16(dst + cdst[m], src + csrc[m]);
+            cp_async_commit();
+        } else {
+            column_prefetch<N, TX, TY, Ix, SWZ>(Qin, slot_of(L), g, ex0, ey0, txv, tyv, zmod(L));
+        }
     };
 
     prefetch(z0 - 1);
@@ -266,12 +305,13 @@ __global__ void __launch_bounds__(
             }
             lf_flux2_f<2>(tp, tm, gamma, gm1, fzp);
         }
-        for (int t = tid; t < LT::XT + LT::YT; t += nthr) {
+        // interface task t: the local Lax-Friedrichs flux at one x or y face point
+        auto task = [&](int t) {
             if (t < LT::XT) {
                 // interface index slowest, so that a warp shares its source
                 const int ai = t / (TY * N2), r = t - ai * (TY * N2);
                 const int row = r / N2, pt = r - row * N2;
-                if (ai > txv || row >= tyv) continue;
+                if (ai > txv || row >= tyv) return;
                 const Ix er = (Ix)g.nx * (ey0 + row) + plane * z;
                 slot_interface<N, TX, TY, 0, Ix, SWZ>(Qin, cur, sH, g, lm, lp, gamma, gm1, ai, row,
                                                  txv, exL + er, exR + er, pt);
@@ -279,11 +319,17 @@ __global__ void __launch_bounds__(
                 const int u = t - LT::XT;
                 const int ai = u / (TX * N2), r = u - ai * (TX * N2);
                 const int cx = r / N2, pt = r - cx * N2;
-                if (ai > tyv || cx >= txv) continue;
+                if (ai > tyv || cx >= txv) return;
                 const Ix ec = ex0 + cx + plane * z;
                 slot_interface<N, TX, TY, 1, Ix, SWZ>(Qin, cur, sH, g, lm, lp, gamma, gm1, ai, cx,
                                                  tyv, ec + (Ix)g.nx * eyL, ec + (Ix)g.nx * eyR, pt);
             }
+        };
+        if constexpr (LineShape<N, V>::UT) {
+#pragma unroll
+            for (int t = tid; t < LT::XT + LT::YT; t += LT::THREADS) task(t);
+        } else {
+            for (int t = tid; t < LT::XT + LT::YT; t += LT::THREADS) task(t);
         }
         if constexpr (DB) {
             // every thread is past P: the slot of layer z is free, and the
