@@ -28,7 +28,8 @@
 #pragma once
 
 // Column cross-sections per N (= p + 1): one thread per z line, 64 to 256
-// threads per CTA.  DB: fluxes and face fluxes double-buffered by layer
+// threads per CTA (measured on GB300; wider ones lose occupancy to shared
+// memory and registers).  DB: fluxes and face fluxes double-buffered by layer
 // parity, so one barrier per layer separates the two phases instead of two.
 // NS: slots in the ring of staged layers (3: the layer two ahead is fetched
 // during a whole layer; 2: during the second phase only, less shared
@@ -48,12 +49,12 @@ template <> struct LineShape<4, 0> : LineDefaults {
     static constexpr int TX = 2, TY = 2, NS = 2;
     static constexpr bool SWZ = true, UT = true;
 };
-template <> struct LineShape<5, 0> : LineDefaults { static constexpr int TX = 2, TY = 2, NS = 2; };
+template <> struct LineShape<5, 0> : LineDefaults { static constexpr int TX = 3, TY = 2, NS = 2; };
 template <> struct LineShape<6, 0> : LineDefaults {
-    static constexpr int TX = 2, TY = 1;
+    static constexpr int TX = 3, TY = 1;
     static constexpr bool UT = true;
 };
-template <> struct LineShape<7, 0> : LineDefaults { static constexpr int TX = 1, TY = 1; };
+template <> struct LineShape<7, 0> : LineDefaults { static constexpr int TX = 2, TY = 1; };
 
 template <int N, int TX, int TY, bool DB = false, int NS = 3>
 struct LineTile {

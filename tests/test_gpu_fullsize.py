@@ -148,3 +148,93 @@ def test_advance_full_fp32_vortex128():
     scale = np.maximum(absI[:5], 1e-3 * absI[:5].max())
     assert np.max(np.abs(I1[:5] - I0[:5]) / scale) < 1e-6
     assert m.last_error() == dg.DG_OK
+
+
+def _patch_rhs(om_cls, Qdev, nel, p, h, centres):
+    """Oracle right-hand side of each listed element of a periodic mesh from
+    its 3x3x3 neighbourhood alone: the neighbourhood, gathered from the
+    device state, is a periodic 3x3x3 oracle mesh of the same element size
+    whose centre element has the same six face neighbours as in the full
+    mesh.  Returns (R, Q) of the centres, shape (5, len(centres), N, N, N)."""
+    import torch
+    nx, ny, nz = nel
+    pm = om_cls(3, 3, 3, p, 0.0, 0.0, 0.0, 3 * h[0], 3 * h[1], 3 * h[2])
+    R, Qc = [], []
+    for e in centres:
+        ex, ey, ez = e % nx, (e // nx) % ny, e // (nx * ny)
+        idx = [((ex + a - 1) % nx) + nx * (((ey + b - 1) % ny) + ny * ((ez + c - 1) % nz))
+               for c in range(3) for b in range(3) for a in range(3)]
+        Qp = Qdev[:, torch.tensor(idx, device=Qdev.device)].double().cpu().numpy()
+        R.append(pm.rhs(Qp)[:, 13])
+        Qc.append(Qp[:, 13])
+    return np.stack(R, axis=1), np.stack(Qc, axis=1)
+
+
+def _fp32_sampled_rhs_check(dg, m, Q, nel, p, L):
+    import torch
+    h = tuple(L / n for n in nel)
+    el = _sample(nel[0] * nel[1] * nel[2], *nel, k=48, seed=5)
+    R = m.rhs(Q)
+    Rg = R[:, torch.tensor(el, device=R.device)].double().cpu().numpy()
+    del R
+    R_or, Qc = _patch_rhs(oracle.Mesh, Q, nel, p, h, el)
+    lam = max(oracle.Mesh(1, 1, 1, p, 0, 0, 0, *h).cfl_dt(Qc[:, i:i + 1], 1.0)[1]
+              for i in range(len(el)))
+    scale = (2 / min(h)) * lam * np.linalg.norm(Qc)
+    assert np.linalg.norm(Rg - R_or) / scale < 2e-6
+
+
+def test_fp32_rhs_sampled_vortex128():
+    """The FP32 bench configuration's right-hand side (default stage kernel)
+    on sampled elements, every kind of periodic wrap included, against the
+    oracle's evaluation of each element's neighbourhood."""
+    dg = dg_module()
+    L = 16.0
+    box = (0.0, 0.0, 0.0, L, L, L)
+    m = dg.Mesh(128, 128, 128, 3, *box, precision=dg.DG_FP32)
+    Q = m.init("vortex", inputs.vortex_params(0, box))
+    _fp32_sampled_rhs_check(dg, m, Q, (128, 128, 128), 3, L)
+    assert m.last_error() == dg.DG_OK
+
+
+def test_fp32_64bit_index_path():
+    """A float mesh with 5 E N^3 >= 2^31 (201 x 179 x 187 elements, p = 3,
+    9 GB per state) runs the kernels' 64-bit index instantiations: the
+    right-hand side on sampled elements against the oracle, one RK step of
+    the line kernel bitwise equal to the node-per-thread column kernel's,
+    dg_advance bitwise equal to the separate calls, integrals conserved."""
+    dg = dg_module()
+    import torch
+    nel, p, L = (201, 179, 187), 3, 16.0
+    assert 5 * nel[0] * nel[1] * nel[2] * (p + 1) ** 3 >= 2 ** 31
+    box = (0.0, 0.0, 0.0, L, L, L)
+    saved = dg.dg_get_stage_kernel(p)
+    try:
+        dg.dg_set_stage_kernel(p, dg.DG_STAGE_LINES)
+        m = dg.Mesh(*nel, p, *box, precision=dg.DG_FP32)
+        Q0 = m.init("vortex", inputs.vortex_params(4, box))
+        _fp32_sampled_rhs_check(dg, m, Q0, nel, p, L)
+        dt = m.cfl_dt(Q0, 0.5)
+        Q = Q0.clone()
+        dQ = torch.zeros_like(Q)
+        m.rk_step(Q, dQ, dt)
+        integ_sep = m.norms(Q)
+        Qb, dQb = Q0.clone(), torch.zeros_like(Q0)
+        dts_b, integ_b = m.advance(Qb, dQb, 0.5, 1)
+        torch.cuda.synchronize()
+        assert torch.equal(dt, dts_b) and torch.equal(Q, Qb) and torch.equal(integ_sep, integ_b[0])
+        del Qb, dQb
+        dg.dg_set_stage_kernel(p, dg.DG_STAGE_COLUMN)
+        Qc = Q0.clone()
+        dQ.zero_()
+        m.rk_step(Qc, dQ, dt)
+        torch.cuda.synchronize()
+        assert torch.equal(Q, Qc)
+        I0 = to_host(m.norms(Q0))
+        I1 = to_host(integ_sep)
+        absI = to_host(m.norms(Q0.abs()))
+        scale = np.maximum(absI[:5], 1e-3 * absI[:5].max())
+        assert np.max(np.abs(I1[:5] - I0[:5]) / scale) < 1e-6
+        assert m.last_error() == dg.DG_OK
+    finally:
+        dg.dg_set_stage_kernel(p, saved)
