@@ -29,18 +29,16 @@
 
 // Column cross-sections per N (= p + 1): one thread per z line, 64 to 256
 // threads per CTA (measured on GB300; wider ones lose occupancy to shared
-// memory and registers).  DB: fluxes and face fluxes double-buffered by layer
-// parity, so one barrier per layer separates the two phases instead of two.
-// NS: slots in the ring of staged layers (3: the layer two ahead is fetched
-// during a whole layer; 2: during the second phase only, less shared
-// memory).  MINB: CTAs per SM the registers are sized for (0: the compiler's
-// choice).  SWZ: swizzled slot layout (slot_pos).  UT: the interface-task
-// loop unrolled (more independent work per thread, more registers).
+// memory and registers).  NS: slots in the ring of staged layers (3: the
+// layer two ahead is fetched during a whole layer; 2: during the second
+// phase only, less shared memory).  SWZ: swizzled slot layout (slot_pos).
+// UT: the interface-task loop unrolled (more independent work per thread,
+// more registers).
 template <int N, int V>
 struct LineShape;
 struct LineDefaults {
-    static constexpr bool DB = false, SWZ = false, UT = false;
-    static constexpr int NS = 3, MINB = 0;
+    static constexpr bool SWZ = false, UT = false;
+    static constexpr int NS = 3;
 };
 template <> struct LineShape<1, 0> : LineDefaults { static constexpr int TX = 16, TY = 16, NS = 2; };
 template <> struct LineShape<2, 0> : LineDefaults { static constexpr int TX = 8, TY = 8, NS = 2; };
@@ -56,7 +54,7 @@ template <> struct LineShape<6, 0> : LineDefaults {
 };
 template <> struct LineShape<7, 0> : LineDefaults { static constexpr int TX = 2, TY = 1; };
 
-template <int N, int TX, int TY, bool DB = false, int NS = 3>
+template <int N, int TX, int TY, int NS = 3>
 struct LineTile {
     using CT = ColTile<N, TX, TY>;  // slot layout and prefetch units
     static constexpr int N2 = N * N, N3 = N * N * N;
@@ -64,9 +62,8 @@ struct LineTile {
     static constexpr int THREADS = ((EPB * N2 + 31) / 32) * 32;
     static constexpr int FSTR = CT::pad16(2 * NF * N3);  // fluxes [x, y][NF][N3] as node lines
     static constexpr int HSTR = CT::HSTR;                // x, y face fluxes [2][NF][N2][(-,+)]
-    static constexpr int NBUF = DB ? 2 : 1;
     static constexpr size_t FLOATS =
-        (size_t)NS * CT::QSLOT + (size_t)NBUF * EPB * (FSTR + HSTR) + CT::OPSF;
+        (size_t)NS * CT::QSLOT + (size_t)EPB * (FSTR + HSTR) + CT::OPSF;
     static constexpr size_t BYTES = FLOATS * sizeof(float);
     static constexpr int XT = (TX + 1) * TY * N2, YT = (TY + 1) * TX * N2;
 };
@@ -127,25 +124,24 @@ __device__ __forceinline__ void slot_interface(const float *__restrict__ Qin, co
 // One column chunk of the stage; MODE and Ix as for column_stage_kernel.
 template <int N, int V, int MODE, typename Ix>
 __global__ void __launch_bounds__(
-    LineTile<N, LineShape<N, V>::TX, LineShape<N, V>::TY, LineShape<N, V>::DB>::THREADS,
-    LineShape<N, V>::MINB)
+    LineTile<N, LineShape<N, V>::TX, LineShape<N, V>::TY, LineShape<N, V>::NS>::THREADS)
     line_stage_kernel(const float *__restrict__ Qin, float *__restrict__ Out,
                       float *__restrict__ dQ, const Ops<float> T, const Geo g, float A, float B,
                       const double *__restrict__ dt, int zchunk)
 {
     constexpr int TX = LineShape<N, V>::TX, TY = LineShape<N, V>::TY;
-    constexpr bool DB = LineShape<N, V>::DB, SWZ = LineShape<N, V>::SWZ;
+    constexpr bool SWZ = LineShape<N, V>::SWZ;
     constexpr int NS = LineShape<N, V>::NS;
-    static_assert(NS == 3 || (NS == 2 && !DB), "two slots need the two-barrier layer");
-    using LT = LineTile<N, TX, TY, DB, NS>;
+    static_assert(NS == 2 || NS == 3, "two or three staging slots");
+    using LT = LineTile<N, TX, TY, NS>;
     using CT = ColTile<N, TX, TY>;
     constexpr int N2 = LT::N2, N3 = LT::N3, EPB = LT::EPB;
     constexpr int FSTR = LT::FSTR, HSTR = LT::HSTR, ESTR = CT::ESTR;
     extern __shared__ __align__(16) float lsm[];
     float *slots = lsm;                            // [NS][QSLOT]
-    float *sF0 = slots + NS * CT::QSLOT;           // [NBUF][EPB][FSTR]
-    float *sH0 = sF0 + LT::NBUF * EPB * FSTR;      // [NBUF][EPB][HSTR]
-    float *sOp = sH0 + LT::NBUF * EPB * HSTR;      // D[3][N][N], Lm[3][N], Lp[3][N], lm[N], lp[N]
+    float *sF = slots + NS * CT::QSLOT;            // [EPB][FSTR]
+    float *sH = sF + EPB * FSTR;                   // [EPB][HSTR]
+    float *sOp = sH + EPB * HSTR;                  // D[3][N][N], Lm[3][N], Lp[3][N], lm[N], lp[N]
 
     const int ncx = (g.nx + TX - 1) / TX, ncy = (g.ny + TY - 1) / TY;
     const int col = (int)(blockIdx.x % (unsigned)(ncx * ncy));
@@ -268,8 +264,6 @@ __global__ void __launch_bounds__(
     for (int z = z0; z < z1; ++z) {
         const float *cur = slot_of(z), *nxt = slot_of(z + 1);
         const Ix e = ex0 + a + (Ix)g.nx * (ey0 + b) + plane * z;
-        float *sF = sF0 + (DB ? (z & 1) * EPB * FSTR : 0);
-        float *sH = sH0 + (DB ? (z & 1) * EPB * HSTR : 0);
 
         // P: node fluxes, the z interface above the line, x and y interfaces
         float qc[NF][N], fz[NF][N], fzp[NF], dq[NF][N];
@@ -332,18 +326,10 @@ __global__ void __launch_bounds__(
         } else {
             for (int t = tid; t < LT::XT + LT::YT; t += LT::THREADS) task(t);
         }
-        if constexpr (DB) {
-            // every thread is past P: the slot of layer z is free, and the
-            // layer z + 2 copies are complete and visible after the barrier
-            cp_async_wait_all();
-            __syncthreads();
-            if (z + 3 <= z1) prefetch(z + 3);
-        } else {
-            __syncthreads();
-            // two slots: the slot of layer z is free once every thread is past P
-            if constexpr (NS == 2)
-                if (z + 2 <= z1) prefetch(z + 2);
-        }
+        __syncthreads();
+        // two slots: the slot of layer z is free once every thread is past P
+        if constexpr (NS == 2)
+            if (z + 2 <= z1) prefetch(z + 2);
 
         // G: derivative, lift, update of the line's nodes
         if (active) {
@@ -384,13 +370,11 @@ __global__ void __launch_bounds__(
 #pragma unroll
             for (int n = 0; n < NF; ++n) fzm[n] = fzp[n];
         }
-        if constexpr (!DB) {
-            // the fluxes, face fluxes and the slot of layer z are free once
-            // every thread is past G
-            cp_async_wait_all();
-            __syncthreads();
-            if constexpr (NS == 3)
-                if (z + 3 <= z1) prefetch(z + 3);
-        }
+        // the fluxes, face fluxes and (three slots) the slot of layer z are
+        // free once every thread is past G
+        cp_async_wait_all();
+        __syncthreads();
+        if constexpr (NS == 3)
+            if (z + 3 <= z1) prefetch(z + 3);
     }
 }
