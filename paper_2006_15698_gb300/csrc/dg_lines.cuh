@@ -33,11 +33,12 @@
 // layer two ahead is fetched during a whole layer; 2: during the second
 // phase only, less shared memory).  SWZ: swizzled slot layout (slot_pos).
 // UT: the interface-task loop unrolled (more independent work per thread,
-// more registers).
+// more registers).  RC: the layer copied row by row (pays where a row is
+// many copies per thread).
 template <int N, int V>
 struct LineShape;
 struct LineDefaults {
-    static constexpr bool SWZ = false, UT = false;
+    static constexpr bool SWZ = false, UT = false, RC = false;
     static constexpr int NS = 3;
 };
 template <> struct LineShape<1, 0> : LineDefaults { static constexpr int TX = 16, TY = 16, NS = 2; };
@@ -52,7 +53,10 @@ template <> struct LineShape<6, 0> : LineDefaults {
     static constexpr int TX = 3, TY = 1;
     static constexpr bool UT = true;
 };
-template <> struct LineShape<7, 0> : LineDefaults { static constexpr int TX = 2, TY = 1; };
+template <> struct LineShape<7, 0> : LineDefaults {
+    static constexpr int TX = 2, TY = 1;
+    static constexpr bool RC = true;
+};
 
 template <int N, int TX, int TY, int NS = 3>
 struct LineTile {
@@ -219,6 +223,25 @@ __global__ void __launch_bounds__(
 #pragma unroll
             for (int m = 0; m < MAXC; ++m)
                 if (cdst[m] >= 0) cp_async16(dst + cdst[m], src + csrc[m]);
+            cp_async_commit();
+        } else if constexpr (LineShape<N, V>::RC) {
+            static_assert(ESTR == N3 && !SWZ, "row copies need unpadded, unswizzled slots");
+            // unpadded slots: each (field, element row) of the layer is one
+            // contiguous run in DRAM and in the slot, copied unit by unit
+            const Ix lay = plane * (Ix)zmod(L);
+            float *dst0 = slot_of(L);
+            const int len = txv * N3 / W;
+#pragma unroll 1
+            for (int row = 0; row < NF * TY; ++row) {
+                const int n = row / TY, bb = row - n * TY;
+                if (bb >= tyv) continue;
+                const float *src = Qin + ((Ix)n * E + ex0 + (Ix)g.nx * (ey0 + bb) + lay) * N3;
+                float *dst = dst0 + (n * EPB + bb * TX) * ESTR;
+                for (int u = tid; u < len; u += LT::THREADS) {
+                    if constexpr (W == 4) cp_async16(dst + 4 * u, src + 4 * u);
+                    else cp_async4(dst + u, src + u);
+                }
+            }
             cp_async_commit();
         } else {
             column_prefetch<N, TX, TY, Ix, SWZ>(Qin, slot_of(L), g, ex0, ey0, txv, tyv, zmod(L));
