@@ -255,7 +255,7 @@ __device__ __forceinline__ void line_task(const float *slot, float *sT, const fl
                                           const float *lp, int el, int ln, int which)
 {
     using CT = ColTile<N, TX, TY>;
-    constexpr int N2 = CT::N2, N3 = CT::N3, EPB = CT::EPB;
+    constexpr int N2 = CT::N2, EPB = CT::EPB;
     const int t1 = ln % N, t2 = ln / N;
     const int base = line_base<N, DIR>(t1, t2);
     float *t = sT + (size_t)el * CT::TSTR;
