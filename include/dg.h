@@ -257,7 +257,13 @@ int dg_get_stage_kernel(int p);
  * persistent launch computes all time steps, then one persistent launch per
  * RK stage runs every tile of every instance (device dispatch on the degree;
  * a second launch per stage only for p = 6 instances, whose tiles need 352
- * threads).  The stages alternate between Q and the batch's second states,
+ * threads).  Instances of at least 2^19 nodes are not in the work list: each
+ * runs the single-mesh stage kernel of its degree (dg_set_stage_kernel) in
+ * launches of its own, on up to four streams the batch owns, forked from
+ * `stream` after the time steps and joined back to it at the end of every
+ * step, so that they overlap one another and the persistent launches; the
+ * results are those of the same mesh stepped alone, bit for bit.  The
+ * stages alternate between Q and the batch's second states,
  * so an even number of steps ends in Q by itself; after an odd number the
  * second states are copied back (one device memcpy per instance).  With
  * use_graph != 0 the launches of two steps (and of one step) are recorded

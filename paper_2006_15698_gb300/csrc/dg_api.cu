@@ -509,6 +509,15 @@ struct dg_batch {
     int threads = 256, grid = 1;    // CFL launches
     bool small = true;              // every instance's offsets fit a 32-bit int
     std::vector<int> direct;        // large instances: launched by themselves
+    // streams the large instances' stage launches run on, concurrently with
+    // each other and with the persistent launches (forked from and joined to
+    // the caller's stream every step); lane_of[k]: the lane of direct[k]
+    static constexpr int kLanes = 4;
+    int nlanes = 0;
+    cudaStream_t lane[kLanes] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kLanes] = {};
+    std::vector<int> lane_of;
     // per size class of the stage kernel: item range, shared memory, grid
     int cbeg[2] = {0, 0}, cend[2] = {0, 0}, cgrid[2] = {1, 1};
     size_t csmem[2] = {0, 0};
@@ -526,6 +535,11 @@ void batch_free(dg_batch *b)
     cudaDeviceSynchronize();
     for (int k = 1; k <= 2; ++k)
         if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+    for (int k = 0; k < dg_batch::kLanes; ++k) {
+        if (b->lane[k]) cudaStreamDestroy(b->lane[k]);
+        if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     for (void *p : b->qt) cudaFree(p);
     cudaFree(b->d_inst);
     cudaFree(b->d_items);
@@ -583,7 +597,7 @@ cudaError_t batch_enqueue(const dg_batch *b, double cfl, int nsteps, cudaStream_
                                  2277821191437.0 / 14882151754819.0};
     const int ni = (int)b->items.size();
     cudaError_t e = cudaSuccess;
-    int parity = 0;  // 0: the state is in Q
+    int parity = 0;  // 0: the state is in Q at the start of the step
     for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
         e = dg::batch_lambda(b->d_items, ni, b->d_inst, parity, b->d_err, b->grid, b->threads, s);
         for (size_t k = 0; k < b->direct.size() && e == cudaSuccess; ++k) {
@@ -591,19 +605,32 @@ cudaError_t batch_enqueue(const dg_batch *b, double cfl, int nsteps, cudaStream_
             e = dg::float_lambda(I.g, parity == 0 ? I.Q : I.Qt, I.lam_bits, b->d_err, s);
         }
         if (e == cudaSuccess) e = dg::batch_dt(b->d_inst, b->n, cfl, s);
-        for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
+        // the large instances' five stages on their lanes, after the time steps
+        if (e == cudaSuccess && b->nlanes > 0) {
+            e = cudaEventRecord(b->fork_ev, s);
+            for (int l = 0; l < b->nlanes && e == cudaSuccess; ++l)
+                e = cudaStreamWaitEvent(b->lane[l], b->fork_ev, 0);
+        }
+        for (size_t k = 0; k < b->direct.size() && e == cudaSuccess; ++k) {
+            const dg::InstDev &I = b->inst[b->direct[k]];
+            for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
+                const int par = parity ^ (st & 1);
+                e = dg::float_stage(I.g, I.T, par == 0 ? I.Q : I.Qt, par == 0 ? I.Qt : I.Q, I.dQ,
+                                    (float)kA[st], (float)kB[st], I.dt, b->lane[b->lane_of[k]]);
+            }
+        }
+        // the small instances' persistent launches on the caller's stream
+        for (int st = 0; st < 5 && e == cudaSuccess; ++st)
             for (int c = 0; c < 2 && e == cudaSuccess; ++c)
                 if (b->cend[c] > b->cbeg[c])
                     e = dg::batch_stage(b->d_items + b->cbeg[c], b->cend[c] - b->cbeg[c],
-                                        b->d_inst, parity, (float)kA[st], (float)kB[st], c,
-                                        b->small, b->cgrid[c], b->csmem[c], s);
-            for (size_t k = 0; k < b->direct.size() && e == cudaSuccess; ++k) {
-                const dg::InstDev &I = b->inst[b->direct[k]];
-                e = dg::float_stage(I.g, I.T, parity == 0 ? I.Q : I.Qt, parity == 0 ? I.Qt : I.Q,
-                                    I.dQ, (float)kA[st], (float)kB[st], I.dt, s);
-            }
-            parity ^= 1;
+                                        b->d_inst, parity ^ (st & 1), (float)kA[st], (float)kB[st],
+                                        c, b->small, b->cgrid[c], b->csmem[c], s);
+        for (int l = 0; l < b->nlanes && e == cudaSuccess; ++l) {
+            e = cudaEventRecord(b->join_ev[l], b->lane[l]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join_ev[l], 0);
         }
+        parity ^= 1;  // five stages
     }
     if (parity == 1)
         for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
@@ -742,6 +769,33 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
         b->cgrid[c] = (int)std::min<long long>((long long)sms * per_sm, cnt);
     }
     b->grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * 8, (long long)ni));
+    // lanes for the large instances: largest first onto the least loaded lane
+    if (!b->direct.empty()) {
+        b->nlanes = (int)std::min<size_t>(dg_batch::kLanes, b->direct.size());
+        std::vector<int> order(b->direct.size());
+        for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return b->dofs[b->direct[x]] > b->dofs[b->direct[y]];
+        });
+        std::vector<long long> load(b->nlanes, 0);
+        b->lane_of.assign(b->direct.size(), 0);
+        for (int k : order) {
+            const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            b->lane_of[k] = l;
+            load[l] += b->dofs[b->direct[k]];
+        }
+        err = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+        for (int l = 0; l < b->nlanes && err == cudaSuccess; ++l) {
+            err = cudaStreamCreateWithFlags(&b->lane[l], cudaStreamNonBlocking);
+            if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->join_ev[l], cudaEventDisableTiming);
+        }
+        if (err != cudaSuccess) {
+            dg_status st = cuda_status(err);
+            cudaGetLastError();
+            batch_free(b);
+            return st;
+        }
+    }
     *out = b;
     return DG_OK;
 }
