@@ -257,7 +257,8 @@ int dg_get_stage_kernel(int p);
  * persistent launch computes all time steps, then one persistent launch per
  * RK stage runs every tile of every instance (device dispatch on the degree;
  * a second launch per stage only for p = 6 instances, whose tiles need 352
- * threads).  Instances of at least 2^19 nodes are not in the work list: each
+ * threads).  Instances of at least dg_get_batch_direct_nodes() nodes
+ * (default 2^13) are not in the work list: each
  * runs the single-mesh stage kernel of its degree (dg_set_stage_kernel) in
  * launches of its own, on up to four streams the batch owns, forked from
  * `stream` after the time steps and joined back to it at the end of every
@@ -274,7 +275,11 @@ int dg_get_stage_kernel(int p);
  * doubles (synchronises); dg_batch_norms writes instance idx's integrals as
  * dg_norms does; dg_batch_state_init fills instance idx's Q like
  * dg_state_init; dg_batch_last_error reads and clears the batch's
- * non-finite flag.  Errors as for dg_mesh_create and dg_rk_step. */
+ * non-finite flag.  Errors as for dg_mesh_create and dg_rk_step.
+ * dg_set_batch_direct_nodes sets that size threshold for batches created
+ * afterwards (process-wide, like the tuning tables; 0: every instance runs its
+ * own launches; INT64_MAX: all share the persistent launches); DG_ERR_ARG for
+ * a negative value. */
 typedef struct {
     int nx, ny, nz, p;
     double x0, y0, z0, Lx, Ly, Lz, gamma;
@@ -286,6 +291,8 @@ typedef struct {
 typedef struct dg_batch dg_batch;
 dg_status dg_batch_create(int n, const dg_instance *instances, dg_batch **out);
 void dg_batch_destroy(dg_batch *batch);
+dg_status dg_set_batch_direct_nodes(int64_t nodes);
+int64_t dg_get_batch_direct_nodes(void);
 dg_status dg_batch_sizes(const dg_batch *batch, int64_t *n_dof, int64_t *n_items);
 dg_status dg_batch_state_init(const dg_batch *batch, int idx, dg_init_kind kind,
                               const double *params, int nparams, void *stream);

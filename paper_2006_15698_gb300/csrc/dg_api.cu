@@ -1,6 +1,7 @@
 // dg_api.cu -- host side of the C ABI declared in include/dg.h: argument
 // checks, the 1D operators of the collocated Gauss-Legendre basis, the mesh
 // handle's device workspace, and dispatch to the per-precision launchers.
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -550,10 +551,11 @@ void batch_free(dg_batch *b)
     delete b;
 }
 
-// Instances of at least this many nodes fill the GPU with their own launches
-// of the single-mesh stage kernels (inside the batch's step and graph); the
-// smaller ones share the persistent batched launches.
-constexpr long long kDirectDof = 1LL << 19;
+// Instances of at least this many nodes run their own launches of the
+// single-mesh stage kernels (inside the batch's step and graph, on the
+// batch's lanes); the smaller ones share the persistent batched launches.
+// Process-wide, read by dg_batch_create (dg_set_batch_direct_nodes).
+std::atomic<long long> g_direct_nodes{1LL << 13};
 
 // Tile variant of order N inside a batch.  The batch runs every tile with one
 // block size (256 threads, 352 when a p = 6 instance is present), so the tile
@@ -665,6 +667,7 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
     }
     dg_batch *b = new (std::nothrow) dg_batch();
     if (!b) return DG_ERR_OOM;
+    const long long direct_nodes = g_direct_nodes.load();
     b->n = n;
     b->inst.resize(n);
     cudaError_t err = cudaSuccess;
@@ -727,7 +730,7 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
             batch_free(b);
             return DG_ERR_UNSUPPORTED;
         }
-        if (b->dofs[i] >= kDirectDof) {  // fills the GPU by itself: own launches
+        if (b->dofs[i] >= direct_nodes) {  // own launches
             b->direct.push_back(i);
             continue;
         }
@@ -801,6 +804,15 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
 }
 
 void dg_batch_destroy(dg_batch *b) { batch_free(b); }
+
+dg_status dg_set_batch_direct_nodes(int64_t nodes)
+{
+    if (nodes < 0) return DG_ERR_ARG;
+    g_direct_nodes.store((long long)nodes);
+    return DG_OK;
+}
+
+int64_t dg_get_batch_direct_nodes(void) { return (int64_t)g_direct_nodes.load(); }
 
 dg_status dg_batch_sizes(const dg_batch *b, int64_t *n_dof, int64_t *n_items)
 {

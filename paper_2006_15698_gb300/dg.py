@@ -96,6 +96,10 @@ _lib.dg_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(DgInstance), ctype
 _lib.dg_batch_create.restype = ctypes.c_int
 _lib.dg_batch_destroy.argtypes = [_vp]
 _lib.dg_batch_destroy.restype = None
+_lib.dg_set_batch_direct_nodes.argtypes = [ctypes.c_int64]
+_lib.dg_set_batch_direct_nodes.restype = ctypes.c_int
+_lib.dg_get_batch_direct_nodes.argtypes = []
+_lib.dg_get_batch_direct_nodes.restype = ctypes.c_int64
 _lib.dg_batch_sizes.argtypes = [_vp, _i64p, _i64p]
 _lib.dg_batch_sizes.restype = ctypes.c_int
 _lib.dg_batch_state_init.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _vp]
@@ -326,6 +330,19 @@ def dg_set_stage_kernel(p, kind):
 
 def dg_get_stage_kernel(p):
     return _lib.dg_get_stage_kernel(p)
+
+
+BATCH_NEVER_DIRECT = 2 ** 63 - 1
+
+
+def dg_set_batch_direct_nodes(nodes):
+    """Batches created afterwards give instances of at least `nodes` nodes
+    their own stage launches (0: all of them; BATCH_NEVER_DIRECT: none)."""
+    _check(_lib.dg_set_batch_direct_nodes(int(nodes)), "dg_set_batch_direct_nodes")
+
+
+def dg_get_batch_direct_nodes():
+    return _lib.dg_get_batch_direct_nodes()
 
 
 TUNING_PATH = os.path.join(_HERE, "tuning", "fused_tiles.json")

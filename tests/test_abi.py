@@ -96,3 +96,10 @@ def test_tuning_tables_validate_on_host(lib):
     assert lib.dg_set_stage_kernel(3, 3) == 1
     lib.dg_set_stage_kernel(3, saved)
     assert lib.dg_set_tile_variant(3, lib.dg_tile_variant_count(3)) == 1
+    lib.dg_set_batch_direct_nodes.argtypes = [ctypes.c_int64]
+    lib.dg_get_batch_direct_nodes.restype = ctypes.c_int64
+    saved = lib.dg_get_batch_direct_nodes()
+    assert saved >= 0
+    assert lib.dg_set_batch_direct_nodes(-1) == 1        # DG_ERR_ARG
+    assert lib.dg_set_batch_direct_nodes(12345) == 0 and lib.dg_get_batch_direct_nodes() == 12345
+    assert lib.dg_set_batch_direct_nodes(saved) == 0

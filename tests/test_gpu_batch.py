@@ -1,7 +1,11 @@
 """Tile variants of the float form's fused stage, and batches of independent
-float meshes (one persistent launch per RK stage, optional CUDA graph).
-(Single meshes default to the column stage kernel; the tests that compare a
-single mesh with a batch bitwise select the tile kernel for it.)
+float meshes (one persistent launch per RK stage for the small instances,
+own launches on the batch's streams for the others, optional CUDA graph).
+The batch tests run with every instance in the persistent launch, with the
+default split and with every instance on its own launches
+(dg_set_batch_direct_nodes).  (Single meshes default to the line stage
+kernel; the tests that compare a single mesh with a batch bitwise select the
+tile kernel for it.)
 
 * every tile variant of every degree gives the oracle's right-hand side
   (FP32 tolerance), also on meshes that tiles cover raggedly;
@@ -28,10 +32,22 @@ BOX = (0.0, 0.0, 0.0, 10.0, 10.0, 10.0)
 def dgm():
     dg = dg_module()
     saved = {p: (dg.dg_get_tile_variant(p), dg.dg_get_stage_kernel(p)) for p in range(0, 7)}
+    direct = dg.dg_get_batch_direct_nodes()
     yield dg
     for p, (v, k) in saved.items():
         dg.dg_set_tile_variant(p, v)
         dg.dg_set_stage_kernel(p, k)
+    dg.dg_set_batch_direct_nodes(direct)
+
+
+DIRECT = ["never", "default", "all"]
+
+
+def _set_direct(dg, mode):
+    if mode == "never":
+        dg.dg_set_batch_direct_nodes(dg.BATCH_NEVER_DIRECT)
+    elif mode == "all":
+        dg.dg_set_batch_direct_nodes(0)
 
 
 @pytest.mark.parametrize("p", range(0, 7))
@@ -63,10 +79,12 @@ def _specs(seed, n):
     return specs
 
 
+@pytest.mark.parametrize("direct", DIRECT)
 @pytest.mark.parametrize("use_graph", [False, True])
-def test_batch_matches_single_meshes(dgm, use_graph):
+def test_batch_matches_single_meshes(dgm, use_graph, direct):
     dg = dgm
     import torch
+    _set_direct(dg, direct)
     for p in range(0, 7):  # single meshes on the batch's tile kernel: bitwise comparable
         dg.dg_set_stage_kernel(p, dg.DG_STAGE_TILE)
     specs = _specs(11, 7)
@@ -114,9 +132,11 @@ def test_batch_instance_against_oracle(dgm):
     assert abs(out[0] - om.norms(Q1)[0]) < 1e-6 * abs(out[0])
 
 
-def test_batch_graph_equals_direct(dgm):
+@pytest.mark.parametrize("direct", DIRECT)
+def test_batch_graph_equals_direct(dgm, direct):
     dg = dgm
     import torch
+    _set_direct(dg, direct)
     specs = _specs(5, 5)
     a, b = dg.Batch(specs), dg.Batch(specs)
     for i in range(len(specs)):
@@ -133,12 +153,14 @@ def test_batch_graph_equals_direct(dgm):
         assert torch.equal(a.Q[i], b.Q[i])
 
 
+@pytest.mark.parametrize("direct", DIRECT)
 @pytest.mark.parametrize("use_graph", [False, True])
-def test_batch_multi_step_call(dgm, use_graph):
+def test_batch_multi_step_call(dgm, use_graph, direct):
     # nsteps in one call (two-step groups ending in Q without a copy, then a
     # last single step with the copy) equals nsteps single-step calls
     dg = dgm
     import torch
+    _set_direct(dg, direct)
     specs = _specs(7, 4)
     a, b = dg.Batch(specs), dg.Batch(specs)
     for i in range(len(specs)):
@@ -175,6 +197,7 @@ def test_hybrid_batch_large_instances_match_single_meshes(dgm, kernel):
     # the large instances' degrees (3, 4) run the kernel under test; the small
     # instances (degrees 2, 5) share the batched tile launch, so their single
     # meshes use the tile kernel too
+    dg.dg_set_batch_direct_nodes(1 << 19)
     for p in range(0, 7):
         big = p in (3, 4)
         dg.dg_set_stage_kernel(p, dg.STAGE_KINDS[kernel] if big else dg.DG_STAGE_TILE)
