@@ -34,11 +34,12 @@
 // phase only, less shared memory).  SWZ: swizzled slot layout (slot_pos).
 // UT: the interface-task loop unrolled (more independent work per thread,
 // more registers).  RC: the layer copied row by row (pays where a row is
-// many copies per thread).
+// many copies per thread).  PFN: the neighbour columns' elements of the next
+// layer prefetched into L2.
 template <int N, int V>
 struct LineShape;
 struct LineDefaults {
-    static constexpr bool SWZ = false, UT = false, RC = false;
+    static constexpr bool SWZ = false, UT = false, RC = false, PFN = false;
     static constexpr int NS = 3;
 };
 template <> struct LineShape<1, 0> : LineDefaults { static constexpr int TX = 16, TY = 16, NS = 2; };
@@ -46,7 +47,7 @@ template <> struct LineShape<2, 0> : LineDefaults { static constexpr int TX = 8,
 template <> struct LineShape<3, 0> : LineDefaults { static constexpr int TX = 4, TY = 4, NS = 2; };
 template <> struct LineShape<4, 0> : LineDefaults {
     static constexpr int TX = 2, TY = 2, NS = 2;
-    static constexpr bool SWZ = true, UT = true;
+    static constexpr bool SWZ = true, UT = true, PFN = true;
 };
 template <> struct LineShape<5, 0> : LineDefaults { static constexpr int TX = 3, TY = 2, NS = 2; };
 template <> struct LineShape<6, 0> : LineDefaults {
@@ -287,6 +288,32 @@ __global__ void __launch_bounds__(
     for (int z = z0; z < z1; ++z) {
         const float *cur = slot_of(z), *nxt = slot_of(z + 1);
         const Ix e = ex0 + a + (Ix)g.nx * (ey0 + b) + plane * z;
+
+        // the neighbour columns' elements of the next layer into L2 (PFN):
+        // their node lines are the interface tasks' only reads from DRAM
+        if constexpr (LineShape<N, V>::PFN) {
+            constexpr int LPE = (N3 * 4 + 127) / 128 + 1;  // cache lines an element spans
+            if (z + 1 < z1) {
+                const Ix zn = plane * (Ix)(z + 1);
+                for (int t = tid; t < NF * 2 * (TX + TY) * LPE; t += LT::THREADS) {
+                    const int n = t / (2 * (TX + TY) * LPE), r = t - n * (2 * (TX + TY) * LPE);
+                    const int k = r / LPE, l = r - k * LPE;
+                    Ix e2;
+                    if (k < 2 * TY) {  // left / right neighbour column's row
+                        const int row = k >> 1;
+                        if (row >= tyv) continue;
+                        e2 = (k & 1 ? exR : exL) + (Ix)g.nx * (ey0 + row) + zn;
+                    } else {           // front / back
+                        const int cx = (k - 2 * TY) >> 1;
+                        if (cx >= txv) continue;
+                        e2 = ex0 + cx + (Ix)g.nx * (k & 1 ? eyR : eyL) + zn;
+                    }
+                    const char *a = reinterpret_cast<const char *>(Qin + ((Ix)n * E + e2) * N3);
+                    const char *q = a + 128 * l;
+                    if (q < a + N3 * sizeof(float)) asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+                }
+            }
+        }
 
         // P: node fluxes, the z interface above the line, x and y interfaces
         float qc[NF][N], fz[NF][N], fzp[NF], dq[NF][N];
