@@ -65,10 +65,13 @@ struct LineTile {
     static constexpr int N2 = N * N, N3 = N * N * N;
     static constexpr int EPB = TX * TY;
     static constexpr int THREADS = ((EPB * N2 + 31) / 32) * 32;
-    static constexpr int FSTR = CT::pad16(2 * NF * N3);  // fluxes [x, y][NF][N3] as node lines
+    // fluxes [x, y][NF][N3] as node lines; element stride = N^2 (mod 32), so
+    // that the N^2 threads of consecutive elements store to consecutive banks
+    static constexpr int FSTR = 2 * NF * N3 + ((N2 - (2 * NF * N3) % 32) % 32 + 32) % 32;
     static constexpr int HSTR = CT::HSTR;                // x, y face fluxes [2][NF][N2][(-,+)]
+    static constexpr int FREG = (EPB * FSTR + 3) / 4 * 4;  // flux region, 16-byte multiple
     static constexpr size_t FLOATS =
-        (size_t)NS * CT::QSLOT + (size_t)EPB * (FSTR + HSTR) + CT::OPSF;
+        (size_t)NS * CT::QSLOT + (size_t)FREG + (size_t)EPB * HSTR + CT::OPSF;
     static constexpr size_t BYTES = FLOATS * sizeof(float);
     static constexpr int XT = (TX + 1) * TY * N2, YT = (TY + 1) * TX * N2;
 };
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(
     extern __shared__ __align__(16) float lsm[];
     float *slots = lsm;                            // [NS][QSLOT]
     float *sF = slots + NS * CT::QSLOT;            // [EPB][FSTR]
-    float *sH = sF + EPB * FSTR;                   // [EPB][HSTR]
+    float *sH = sF + LT::FREG;                     // [EPB][HSTR]
     float *sOp = sH + EPB * HSTR;                  // D[3][N][N], Lm[3][N], Lp[3][N], lm[N], lp[N]
 
     const int ncx = (g.nx + TX - 1) / TX, ncy = (g.ny + TY - 1) / TY;
