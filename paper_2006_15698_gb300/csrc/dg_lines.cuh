@@ -68,10 +68,14 @@ struct LineTile {
     // fluxes [x, y][NF][N3] as node lines; element stride = N^2 (mod 32), so
     // that the N^2 threads of consecutive elements store to consecutive banks
     static constexpr int FSTR = 2 * NF * N3 + ((N2 - (2 * NF * N3) % 32) % 32 + 32) % 32;
-    static constexpr int HSTR = CT::HSTR;                // x, y face fluxes [2][NF][N2][(-,+)]
-    static constexpr int FREG = (EPB * FSTR + 3) / 4 * 4;  // flux region, 16-byte multiple
-    static constexpr size_t FLOATS =
-        (size_t)NS * CT::QSLOT + (size_t)FREG + (size_t)EPB * HSTR + CT::OPSF;
+    // x, y face fluxes [2][NF][N2][(-,+)]; element stride = 2N (mod 32)
+    // (even), so that the N (-,+) pairs each element reads at a time fall into
+    // consecutive banks for consecutive elements (N = 4: the column layout's)
+    static constexpr int HSTR =
+        N == 4 ? CT::HSTR : 4 * NF * N2 + ((2 * N - (4 * NF * N2) % 32) % 32 + 32) % 32;
+    static constexpr int FREG = (EPB * FSTR + 3) / 4 * 4;  // regions in 16-byte multiples
+    static constexpr int HREG = (EPB * HSTR + 3) / 4 * 4;
+    static constexpr size_t FLOATS = (size_t)NS * CT::QSLOT + (size_t)FREG + (size_t)HREG + CT::OPSF;
     static constexpr size_t BYTES = FLOATS * sizeof(float);
     static constexpr int XT = (TX + 1) * TY * N2, YT = (TY + 1) * TX * N2;
 };
@@ -149,7 +153,7 @@ __global__ void __launch_bounds__(
     float *slots = lsm;                            // [NS][QSLOT]
     float *sF = slots + NS * CT::QSLOT;            // [EPB][FSTR]
     float *sH = sF + LT::FREG;                     // [EPB][HSTR]
-    float *sOp = sH + EPB * HSTR;                  // D[3][N][N], Lm[3][N], Lp[3][N], lm[N], lp[N]
+    float *sOp = sH + LT::HREG;                    // D[3][N][N], Lm[3][N], Lp[3][N], lm[N], lp[N]
 
     const int ncx = (g.nx + TX - 1) / TX, ncy = (g.ny + TY - 1) / TY;
     const int col = (int)(blockIdx.x % (unsigned)(ncx * ncy));
