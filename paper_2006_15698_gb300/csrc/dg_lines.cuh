@@ -134,6 +134,8 @@ __device__ __forceinline__ void slot_interface(const float *__restrict__ Qin, co
 }
 
 // One column chunk of the stage; MODE and Ix as for column_stage_kernel.
+// Launched with exactly LineTile::THREADS threads (launch_column_ix): the
+// copy offsets and the interface-task loop stride assume that block size.
 template <int N, int V, int MODE, typename Ix>
 __global__ void __launch_bounds__(
     LineTile<N, LineShape<N, V>::TX, LineShape<N, V>::TY, LineShape<N, V>::NS>::THREADS)
