@@ -201,8 +201,9 @@ def test_fp32_64bit_index_path():
     """A float mesh with 5 E N^3 >= 2^31 (201 x 179 x 187 elements, p = 3,
     9 GB per state) runs the kernels' 64-bit index instantiations: the
     right-hand side on sampled elements against the oracle, one RK step of
-    the line kernel bitwise equal to the node-per-thread column kernel's,
-    dg_advance bitwise equal to the separate calls, integrals conserved."""
+    the line kernel bitwise equal to the node-per-thread column kernel's and
+    to float rounding equal to the tile kernel's, dg_advance bitwise equal
+    to the separate calls, integrals conserved."""
     dg = dg_module()
     import torch
     nel, p, L = (201, 179, 187), 3, 16.0
@@ -230,6 +231,15 @@ def test_fp32_64bit_index_path():
         m.rk_step(Qc, dQ, dt)
         torch.cuda.synchronize()
         assert torch.equal(Q, Qc)
+        # the tile kernel's 64-bit instantiation: same step to float rounding
+        dg.dg_set_stage_kernel(p, dg.DG_STAGE_TILE)
+        dQ.zero_()
+        Qc.copy_(Q0)
+        m.rk_step(Qc, dQ, dt)
+        torch.cuda.synchronize()
+        rel = float(torch.linalg.vector_norm((Qc - Q).double()) / torch.linalg.vector_norm(Q.double()))
+        assert rel < 2e-7, rel
+        del Qc
         I0 = to_host(m.norms(Q0))
         I1 = to_host(integ_sep)
         absI = to_host(m.norms(Q0.abs()))
