@@ -922,7 +922,7 @@ cudaError_t launch_column_ix(const Geo &g, const Ops<float> &T, const float *Qin
 {
     constexpr int TX = LINES ? LineShape<N, 0>::TX : ColShape<N, 0>::TX;
     constexpr int TY = LINES ? LineShape<N, 0>::TY : ColShape<N, 0>::TY;
-    using LT = LineTile<N, TX, TY, LineShape<N, 0>::NS>;
+    using LT = LineTile<N, TX, TY, LineShape<N, 0>::NS, LineShape<N, 0>::RPAD>;
     constexpr int THREADS = LINES ? LT::THREADS : ColTile<N, TX, TY>::THREADS;
     constexpr size_t BYTES = LINES ? LT::BYTES : ColTile<N, TX, TY>::BYTES;
     auto kernel = LINES ? line_stage_kernel<N, 0, MODE, Ix> : column_stage_kernel<N, 0, MODE, Ix>;

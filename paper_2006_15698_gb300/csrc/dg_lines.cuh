@@ -35,15 +35,17 @@
 // UT: the interface-task loop unrolled (more independent work per thread,
 // more registers).  RC: the layer copied row by row (pays where a row is
 // many copies per thread).  PFN: the neighbour columns' elements of the next
-// layer prefetched into L2.
+// layer prefetched into L2.  RPAD: floats of padding after every element row
+// of a slot, so that the rows of one x-interface task batch fall into
+// different banks (where a row is a multiple of 32 floats).
 template <int N, int V>
 struct LineShape;
 struct LineDefaults {
     static constexpr bool SWZ = false, UT = false, RC = false, PFN = false;
-    static constexpr int NS = 3;
+    static constexpr int NS = 3, RPAD = 0;
 };
-template <> struct LineShape<1, 0> : LineDefaults { static constexpr int TX = 16, TY = 16, NS = 2; };
-template <> struct LineShape<2, 0> : LineDefaults { static constexpr int TX = 8, TY = 8, NS = 2; };
+template <> struct LineShape<1, 0> : LineDefaults { static constexpr int TX = 16, TY = 16, NS = 2, RPAD = 1; };
+template <> struct LineShape<2, 0> : LineDefaults { static constexpr int TX = 8, TY = 8, NS = 2, RPAD = 8; };
 template <> struct LineShape<3, 0> : LineDefaults { static constexpr int TX = 4, TY = 4, NS = 2; };
 template <> struct LineShape<4, 0> : LineDefaults {
     static constexpr int TX = 2, TY = 2, NS = 2;
@@ -59,9 +61,9 @@ template <> struct LineShape<7, 0> : LineDefaults {
     static constexpr bool RC = true;
 };
 
-template <int N, int TX, int TY, int NS = 3>
+template <int N, int TX, int TY, int NS = 3, int RPAD = 0>
 struct LineTile {
-    using CT = ColTile<N, TX, TY>;  // slot layout and prefetch units
+    using CT = ColTile<N, TX, TY>;  // element layout in a slot, prefetch units
     static constexpr int N2 = N * N, N3 = N * N * N;
     static constexpr int EPB = TX * TY;
     static constexpr int THREADS = ((EPB * N2 + 31) / 32) * 32;
@@ -75,22 +77,30 @@ struct LineTile {
         N == 4 ? CT::HSTR : 4 * NF * N2 + ((2 * N - (4 * NF * N2) % 32) % 32 + 32) % 32;
     static constexpr int FREG = (EPB * FSTR + 3) / 4 * 4;  // regions in 16-byte multiples
     static constexpr int HREG = (EPB * HSTR + 3) / 4 * 4;
-    static constexpr size_t FLOATS = (size_t)NS * CT::QSLOT + (size_t)FREG + (size_t)HREG + CT::OPSF;
+    // a slot: [NF][TY] element rows of TX elements (ESTR apart), RSTR apart
+    static constexpr int RSTR = TX * CT::ESTR + RPAD;
+    static constexpr int QSLOT = (NF * TY * RSTR + 3) / 4 * 4;
+    static constexpr size_t FLOATS = (size_t)NS * QSLOT + (size_t)FREG + (size_t)HREG + CT::OPSF;
+    // offset of field n of slot element el (= b * TX + a)
+    __device__ static constexpr int eoff(int n, int el)
+    {
+        if constexpr (RPAD == 0) return (n * EPB + el) * CT::ESTR;
+        else return (n * TY + el / TX) * RSTR + (el % TX) * CT::ESTR;
+    }
     static constexpr size_t BYTES = FLOATS * sizeof(float);
     static constexpr int XT = (TX + 1) * TY * N2, YT = (TY + 1) * TX * N2;
 };
 
 // trace of a staged node line (element el of the slot) at one end; base is
 // the line's first node (line_base)
-template <int N, int TX, int TY, int DIR, bool SWZ>
+template <class LT, int N, int DIR, bool SWZ>
 __device__ __forceinline__ void slot_trace(const float *slot, int el, int base, const float *l,
                                            float q[NF])
 {
-    using CT = ColTile<N, TX, TY>;
     constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? N : N * N);
 #pragma unroll
     for (int n = 0; n < NF; ++n) {
-        const float *e = slot + (n * CT::EPB + el) * CT::ESTR;
+        const float *e = slot + LT::eoff(n, el);
         float v[N];
         if constexpr (DIR == 0) {
             load_line<N>(e + slot_pos<N, SWZ>(base), v);   // an x line is one 16-byte unit
@@ -104,21 +114,20 @@ __device__ __forceinline__ void slot_trace(const float *slot, int el, int base, 
 
 // x (DIR 0) or y (DIR 1) interface a in [0, len] of row r at face point pt,
 // both traces from node lines (staged, or the neighbour column's in DRAM/L2)
-template <int N, int TX, int TY, int DIR, typename Ix, bool SWZ>
+template <class LT, int N, int TX, int TY, int DIR, typename Ix, bool SWZ>
 __device__ __forceinline__ void slot_interface(const float *__restrict__ Qin, const float *slot,
                                                float *sH, const Geo &g, const float *lm,
                                                const float *lp, float gamma, float gm1, int a,
                                                int r, int len, Ix e_lo, Ix e_hi, int pt)
 {
-    using LT = LineTile<N, TX, TY>;
     constexpr int N2 = LT::N2;
     const int base = line_base<N, DIR>(pt % N, pt / N);
     auto local = [&](int c) { return DIR == 0 ? r * TX + c : c * TX + r; };
     float qL[NF], qR[NF];
     if (a == 0) global_trace<N, DIR, Ix>(Qin, (Ix)g.E, e_lo, base, lp, qL);
-    else slot_trace<N, TX, TY, DIR, SWZ>(slot, local(a - 1), base, lp, qL);
+    else slot_trace<LT, N, DIR, SWZ>(slot, local(a - 1), base, lp, qL);
     if (a == len) global_trace<N, DIR, Ix>(Qin, (Ix)g.E, e_hi, base, lm, qR);
-    else slot_trace<N, TX, TY, DIR, SWZ>(slot, local(a), base, lm, qR);
+    else slot_trace<LT, N, DIR, SWZ>(slot, local(a), base, lm, qR);
     float f[NF];
     lf_flux2_f<DIR>(qL, qR, gamma, gm1, f);
     if (a > 0) {
@@ -138,7 +147,8 @@ __device__ __forceinline__ void slot_interface(const float *__restrict__ Qin, co
 // copy offsets and the interface-task loop stride assume that block size.
 template <int N, int V, int MODE, typename Ix>
 __global__ void __launch_bounds__(
-    LineTile<N, LineShape<N, V>::TX, LineShape<N, V>::TY, LineShape<N, V>::NS>::THREADS)
+    LineTile<N, LineShape<N, V>::TX, LineShape<N, V>::TY, LineShape<N, V>::NS,
+             LineShape<N, V>::RPAD>::THREADS)
     line_stage_kernel(const float *__restrict__ Qin, float *__restrict__ Out,
                       float *__restrict__ dQ, const Ops<float> T, const Geo g, float A, float B,
                       const double *__restrict__ dt, int zchunk)
@@ -147,13 +157,13 @@ __global__ void __launch_bounds__(
     constexpr bool SWZ = LineShape<N, V>::SWZ;
     constexpr int NS = LineShape<N, V>::NS;
     static_assert(NS == 2 || NS == 3, "two or three staging slots");
-    using LT = LineTile<N, TX, TY, NS>;
+    using LT = LineTile<N, TX, TY, NS, LineShape<N, V>::RPAD>;
     using CT = ColTile<N, TX, TY>;
     constexpr int N2 = LT::N2, N3 = LT::N3, EPB = LT::EPB;
     constexpr int FSTR = LT::FSTR, HSTR = LT::HSTR, ESTR = CT::ESTR;
     extern __shared__ __align__(16) float lsm[];
     float *slots = lsm;                            // [NS][QSLOT]
-    float *sF = slots + NS * CT::QSLOT;            // [EPB][FSTR]
+    float *sF = slots + NS * LT::QSLOT;            // [EPB][FSTR]
     float *sH = sF + LT::FREG;                     // [EPB][HSTR]
     float *sOp = sH + LT::HREG;                    // D[3][N][N], Lm[3][N], Lp[3][N], lm[N], lp[N]
 
@@ -190,7 +200,7 @@ __global__ void __launch_bounds__(
     const bool active = el < EPB && a < txv && b < tyv;
     const int i = ln % N, j = ln / N;
 
-    auto slot_of = [&](int L) { return slots + ((L - z0 + 1) % NS) * CT::QSLOT; };
+    auto slot_of = [&](int L) { return slots + ((L - z0 + 1) % NS) * LT::QSLOT; };
     auto zmod = [&](int L) { return (L % g.nz + g.nz) % g.nz; };
     // node line (i, j) of this thread's element in a slot, per field
     auto load_zline = [&](const float *slot, float v[NF][N]) {
@@ -198,7 +208,7 @@ __global__ void __launch_bounds__(
         for (int n = 0; n < NF; ++n)
 #pragma unroll
             for (int c = 0; c < N; ++c)
-                v[n][c] = slot[(n * EPB + el) * ESTR + slot_pos<N, SWZ>((c * N + j) * N + i)];
+                v[n][c] = slot[LT::eoff(n, el) + slot_pos<N, SWZ>((c * N + j) * N + i)];
     };
     // This thread's share of a layer's copy: the same units every layer, so
     // their offsets (source relative to the layer, destination relative to
@@ -222,7 +232,7 @@ __global__ void __launch_bounds__(
             if (t < UNITS && bb < tyv && u * W < txv * N3) {
                 const int ea = (u * W) / N3, o = u * W - ea * N3;
                 csrc[m] = ((Ix)n * E + ex0 + (Ix)g.nx * (ey0 + bb)) * N3 + u * W;
-                cdst[m] = (n * EPB + bb * TX + ea) * ESTR + slot_pos<N, SWZ>(o);
+                cdst[m] = LT::eoff(n, bb * TX + ea) + slot_pos<N, SWZ>(o);
             }
         }
     }
@@ -246,15 +256,32 @@ __global__ void __launch_bounds__(
                 const int n = row / TY, bb = row - n * TY;
                 if (bb >= tyv) continue;
                 const float *src = Qin + ((Ix)n * E + ex0 + (Ix)g.nx * (ey0 + bb) + lay) * N3;
-                float *dst = dst0 + (n * EPB + bb * TX) * ESTR;
+                float *dst = dst0 + LT::eoff(n, bb * TX);
                 for (int u = tid; u < len; u += LT::THREADS) {
                     if constexpr (W == 4) cp_async16(dst + 4 * u, src + 4 * u);
                     else cp_async4(dst + u, src + u);
                 }
             }
             cp_async_commit();
-        } else {
+        } else if constexpr (LineShape<N, V>::RPAD == 0) {
             column_prefetch<N, TX, TY, Ix, SWZ>(Qin, slot_of(L), g, ex0, ey0, txv, tyv, zmod(L));
+        } else {
+            // the column kernel's unit loop, into the padded rows
+            const Ix lay = plane * (Ix)zmod(L);
+            float *dst0 = slot_of(L);
+            for (int t = tid; t < UNITS; t += LT::THREADS) {
+                const int n = t / (TY * RU);
+                const int r = t - n * (TY * RU);
+                const int bb = r / RU;
+                const int u = r - bb * RU;
+                if (bb >= tyv || u * W >= txv * N3) continue;
+                const int ea = (u * W) / N3, o = u * W - ea * N3;
+                const float *src = Qin + ((Ix)n * E + ex0 + (Ix)g.nx * (ey0 + bb) + lay) * N3 + u * W;
+                float *dst = dst0 + LT::eoff(n, bb * TX + ea) + slot_pos<N, SWZ>(o);
+                if constexpr (W == 4) cp_async16(dst, src);
+                else cp_async4(dst, src);
+            }
+            cp_async_commit();
         }
     };
 
@@ -367,7 +394,7 @@ __global__ void __launch_bounds__(
                 const int row = r / N2, pt = r - row * N2;
                 if (ai > txv || row >= tyv) return;
                 const Ix er = (Ix)g.nx * (ey0 + row) + plane * z;
-                slot_interface<N, TX, TY, 0, Ix, SWZ>(Qin, cur, sH, g, lm, lp, gamma, gm1, ai, row,
+                slot_interface<LT, N, TX, TY, 0, Ix, SWZ>(Qin, cur, sH, g, lm, lp, gamma, gm1, ai, row,
                                                  txv, exL + er, exR + er, pt);
             } else {
                 const int u = t - LT::XT;
@@ -375,7 +402,7 @@ __global__ void __launch_bounds__(
                 const int cx = r / N2, pt = r - cx * N2;
                 if (ai > tyv || cx >= txv) return;
                 const Ix ec = ex0 + cx + plane * z;
-                slot_interface<N, TX, TY, 1, Ix, SWZ>(Qin, cur, sH, g, lm, lp, gamma, gm1, ai, cx,
+                slot_interface<LT, N, TX, TY, 1, Ix, SWZ>(Qin, cur, sH, g, lm, lp, gamma, gm1, ai, cx,
                                                  tyv, ec + (Ix)g.nx * eyL, ec + (Ix)g.nx * eyR, pt);
             }
         };
