@@ -103,3 +103,25 @@ def test_tuning_tables_validate_on_host(lib):
     assert lib.dg_set_batch_direct_nodes(-1) == 1        # DG_ERR_ARG
     assert lib.dg_set_batch_direct_nodes(12345) == 0 and lib.dg_get_batch_direct_nodes() == 12345
     assert lib.dg_set_batch_direct_nodes(saved) == 0
+
+
+def test_committed_tuning_table_applies():
+    """The autotuner table shipped with the package names only known stage
+    kernels and tile variants in range, and dg.load_tuning applies exactly
+    those choices to the process-wide tables (host-only calls)."""
+    from paper_2006_15698_gb300 import dg
+    saved = {p: (dg.dg_get_tile_variant(p), dg.dg_get_stage_kernel(p)) for p in range(7)}
+    try:
+        table = dg.load_tuning()
+        assert table is not None and table["degrees"]
+        for p, ent in table["degrees"].items():
+            p = int(p)
+            assert ent["kernel"] in dg.STAGE_KINDS, ent
+            assert 0 <= int(ent["variant"]) < dg.dg_tile_variant_count(p), ent
+            assert dg.dg_get_stage_kernel(p) == dg.STAGE_KINDS[ent["kernel"]]
+            assert dg.dg_get_tile_variant(p) == int(ent["variant"])
+            assert list(dg.dg_tile_shape(p, int(ent["variant"]))) == list(ent["tile"])
+    finally:
+        for p, (v, k) in saved.items():
+            dg.dg_set_tile_variant(p, v)
+            dg.dg_set_stage_kernel(p, k)
