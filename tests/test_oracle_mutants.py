@@ -46,7 +46,13 @@ MUTANTS = {
     "vortex_velocity_sign": ("u = ui - beta / (2.0 * pi) * dy * g;", "u = ui + beta / (2.0 * pi) * dy * g;"),
     "sound_speed_gamma_dropped": ("double cL = sqrt(gamma * pressure(qL, gamma) / qL[0]);",
                                   "double cL = sqrt(pressure(qL, gamma) / qL[0]);"),
+    # a wrong quadrature weight in the brute-force volume sums only
+    "o1_volume_weight": ("double wq = J * w[a] * w[bq] * w[c];",
+                         "double wq = J * w[a] * w[a] * w[c];"),
 }
+
+# pins that must be among the failures of a given mutant
+MUST_CATCH = {"o1_volume_weight": "quadrature_exact"}
 
 
 def _build(name):
@@ -109,6 +115,17 @@ def _checks(lib):
         return np.linalg.norm(R1 - R2) < 1e-12 * np.linalg.norm(R2)
 
     check("o1_equals_o2", o1_o2)
+
+    def quadrature_exact():
+        # continuous polynomial data with a uniform velocity: R = -div F
+        # exactly (tests/test_oracle_rhs.py, quadrature exactness)
+        from test_oracle_rhs import _exact_case
+        nel, p, box = (2, 1, 2), 3, (0.0, 0.0, 0.0, 1.3, 0.8, 1.1)
+        mm = oracle.Mesh(*nel, p, *box, lib=lib)
+        Q, R, scale = _exact_case(nel, p, box, 3)
+        return all(np.max(np.abs(mm.rhs(Q, form) - R)) < 2e-15 * scale for form in ("o1", "o2"))
+
+    check("quadrature_exact", quadrature_exact)
 
     def p0_fv():
         mm = oracle.Mesh(3, 1, 1, 0, Lx=1.5, Ly=1.0, Lz=1.0, lib=lib)
@@ -182,3 +199,5 @@ def test_planted_mistake_is_caught(name):
         assert failed == [], failed
     else:
         assert failed, f"mutant {name} passed every pin"
+        if name in MUST_CATCH:
+            assert MUST_CATCH[name] in failed, (name, failed)
