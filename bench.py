@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -38,6 +39,11 @@ WORKLOADS = {
                               init="vortex", params=None, prec="fp32", cfl=0.5,
                               desc="isentropic vortex (seed 0) on a periodic 16^3 box, 128^3 hex "
                                    "elements, p=3, FP32 state and arithmetic, FP64 reductions"),
+    # the headline problem in the FP32 bulk form (FP32 / FP64 on equal terms)
+    "tgv64_p4_fp32": dict(nel=(64, 64, 64), p=4, box=(0, 0, 0, TWO_PI, TWO_PI, TWO_PI),
+                          init="tgv", params=[1.0, 1.0, 0.1], prec="fp32", cfl=0.5,
+                          desc="inviscid Taylor-Green vortex, Mach 0.1, periodic [0,2pi]^3, "
+                               "64^3 hex elements, p=4, FP32 state and arithmetic, FP64 reductions"),
     # small cases (profiling captures, quick checks)
     "tgv32_p4_fp64": dict(nel=(32, 32, 32), p=4, box=(0, 0, 0, TWO_PI, TWO_PI, TWO_PI),
                           init="tgv", params=[1.0, 1.0, 0.1], prec="fp64", cfl=0.5,
@@ -204,11 +210,39 @@ def run_batch(args, w):
 METRIC = "DOF-updates/s per RK stage"
 UNIT = "DOF-stage/s"
 
-# FP64 peak of the GB300 CUDA cores, derived from unit counts and clock: NVIDIA's
-# nominal 1.25 TFLOP/s FP64 at the 2070 MHz maximum SM clock is 4 flop per SM
-# per clock (2 FP64 FMA lanes per SM) x 152 SMs.
-FP64_PEAK_TFLOPS = 1.25
-FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.070e9 / 1e12  # 128 FP32 FMA lanes/SM at max clock
+
+def _sm_clock_mhz(index):
+    """(current, maximum) SM clock of GPU `index` in MHz from nvidia-smi, or None."""
+    try:
+        r = subprocess.run(["nvidia-smi", f"--id={index}", "--query-gpu=clocks.sm,clocks.max.sm",
+                            "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                           timeout=10)
+        cur, mx = (float(x) for x in r.stdout.strip().split(",")[:2])
+        return cur, mx
+    except Exception:
+        return None
+
+
+def fp64_peak(dg):
+    """Roofline denominator of the FP64-pipe-bound kernels, derived from unit
+    counts and clocks: FP64 FMA issue slots per SM per clock (the library's
+    FMA probe, dg_fma_throughput, divided by SM count x the SM clock seen just
+    after it, rounded to whole slots) x 2 flop x SM count (queried) x the
+    maximum SM clock.  Also returns the probe's own rate."""
+    import torch
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    flops, _ = dg.dg_fma_throughput(dg.DG_FP64)
+    clk = _sm_clock_mhz(dev)
+    peaks, _ = _peaks()
+    cur, mx = clk if clk else (peaks.get("sm_max_mhz", 2070.0),) * 2
+    per_clk = flops / (sms * cur * 1e6)
+    slots = max(1, round(per_clk / 2.0))
+    peak = slots * 2.0 * sms * mx * 1e6 / 1e12
+    return {"peak": peak, "probe_tflops": flops / 1e12, "probe_flop_per_clk_per_sm": per_clk,
+            "fma_per_clk_per_sm": slots, "sms": sms, "sm_max_mhz": mx,
+            "source": f"derived: {slots} FP64 FMA/clk/SM (library FMA probe: {per_clk:.2f} "
+                      f"flop/clk/SM at {cur:.0f} MHz) x 2 flop x {sms} SMs x {mx:.0f} MHz"}
 
 
 def kernel_flops(kind, N, E):
@@ -257,8 +291,8 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv") \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/dg_clocks_{os.getpid()}.csv"
+        fd, self.path = tempfile.mkstemp(prefix=f"dg_clocks_{index}_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
@@ -280,10 +314,15 @@ class ClockSampler:
             self.proc.kill()
         self.fh.close()
         rows = []
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) >= 9:
-                rows.append(f)
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -390,7 +429,7 @@ def run_reference(args, w):
     out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": _config(w, args.workload),
+           "data": "synthetic", "config": _config(w, args.workload, ws),
            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"{args.steps} LSERK45 steps (CFL + 5 stages + integrals) of "
                                       f"the same problem on a {nel[0]}x{nel[1]}x{nel[2]}-element "
@@ -400,19 +439,24 @@ def run_reference(args, w):
     return 0
 
 
-def _config(w, name):
+def _config(w, name, ws=1):
+    """The workload's configuration, the same dict in both arms."""
     nx, ny, nz = w["nel"]
     N = w["p"] + 1
+    dof = nx * ny * nz * N ** 3
+    state_gb = 5 * dof * (8 if w["prec"] == "fp64" else 4) / 1e9
     return {"workload": f"{name}: {w['desc']}; one step = CFL reduction + LSERK45 step + integrals",
-            "elements": nx * ny * nz, "p": w["p"], "dof": nx * ny * nz * N ** 3,
-            "unknowns": 5 * nx * ny * nz * N ** 3, "cfl": w["cfl"], "precision": w["prec"]}
+            "elements": nx * ny * nz, "p": w["p"], "dof": dof,
+            "unknowns": 5 * dof, "cfl": w["cfl"], "precision": w["prec"],
+            "parallelism": f"replicas x{ws}",
+            "l2": f"state arrays {state_gb:.2f} GB each, larger than the 129 MB L2"}
 
 
 # ----------------------------------------------------------------------------
 # GPU run
 # ----------------------------------------------------------------------------
 
-def run_native(args, w):
+def run_native(args, w, with_e2e=True):
     import torch
     import torch.distributed as dist
 
@@ -468,9 +512,10 @@ def run_native(args, w):
     value, ms_max = whole_job_rate(ms, dof * 5 * args.steps, device="cuda")
 
     # ---- end-to-end through host buffers: H2D state, step, D2H state + integrals
-    e2e_steps = max(1, min(args.steps, 10))
-    Qh = torch.empty(Q.shape, dtype=Q.dtype, pin_memory=True)
-    Qh.copy_(Q)
+    e2e_steps = max(1, min(args.steps, 10)) if with_e2e else 0
+    Qh = torch.empty(Q.shape if e2e_steps else (1,), dtype=Q.dtype, pin_memory=True)
+    if e2e_steps:
+        Qh.copy_(Q)
     integ_h = torch.empty(dg.DG_NORMS_LEN, dtype=torch.float64, pin_memory=True)
     torch.cuda.synchronize()
     if ws > 1:
@@ -485,7 +530,9 @@ def run_native(args, w):
         integ_h.copy_(integ[0], non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_val, _ = whole_job_rate(e0.elapsed_time(e1), dof * 5 * e2e_steps, device="cuda")
+    e2e_val = None
+    if e2e_steps:
+        e2e_val, _ = whole_job_rate(e0.elapsed_time(e1), dof * 5 * e2e_steps, device="cuda")
 
     out = None
     if rank == 0:
@@ -497,9 +544,10 @@ def run_native(args, w):
         avg_s = prof[dom][0] / prof[dom][1] / 1e3
         if prec == dg.DG_FP64:
             ach = kernel_flops(dom, N, E) / avg_s / 1e12
-            roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS,
-                    "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
+            pk = fp64_peak(dg)
+            roof = {"bound": "alu", "achieved": ach, "peak": pk["peak"], "unit": "TFLOP/s",
+                    "frac": ach / pk["peak"], "peak_source": pk["source"],
+                    "probe_tflops": pk["probe_tflops"], "frac_of_probe": ach / pk["probe_tflops"],
                     "kernel": dom}
         else:
             gbs = kernel_bytes(dom, N, E, esz) / avg_s / 1e9
@@ -525,8 +573,7 @@ def run_native(args, w):
                "scaling": "weak", "vs_baseline": None,
                "dtype": "f64" if prec == dg.DG_FP64 else "f32",
                "data": "synthetic",
-               "config": dict(_config(w, args.workload), parallelism=f"replicas x{ws}",
-                              l2=f"state arrays {m.state_bytes / 1e9:.2f} GB each, larger than the 129 MB L2"),
+               "config": _config(w, args.workload, ws),
                "roofline": roof, "gpu_launches": launches, "kernels": kernels,
                "e2e": {"value": e2e_val, "unit": UNIT, "steps": e2e_steps,
                        "h2d_bytes_per_step": m.state_bytes,
@@ -539,6 +586,44 @@ def run_native(args, w):
     return out
 
 
+def run_extras(args, headline):
+    """The other forms of the metric on one GPU, measured in the same run as
+    the headline: the FP32 bulk form at its own workload (128^3 p = 3) and at
+    the headline's (64^3 p = 4, for the FP32 / FP64 ratio on equal terms), the
+    batched form (256 uneven instances) and the serving loop (200 requests).
+    Each is timed like the headline (CUDA events, warm-up first, clocks
+    sampled); their throughputs are DOF-stage/s like `value`."""
+    import argparse as _ap
+    extras = {}
+
+    def sub(name, steps=None, warmup=None):
+        return _ap.Namespace(**dict(vars(args), workload=name,
+                                    steps=steps or args.steps, warmup=warmup or args.warmup))
+
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "roofline", "clocks",
+            "device_error_flag", "gpu_launches")
+    r = run_native(sub("vortex128_p3_fp32"), WORKLOADS["vortex128_p3_fp32"], with_e2e=False)
+    extras["fp32_vortex128_p3"] = dict({k: r.get(k) for k in keep},
+                                       workload=r["config"]["workload"])
+    r = run_native(sub("tgv64_p4_fp32"), WORKLOADS["tgv64_p4_fp32"], with_e2e=False)
+    extras["fp32_tgv64_p4"] = dict({k: r.get(k) for k in keep}, workload=r["config"]["workload"],
+                                   fp32_over_fp64_same_config=r["value"] / headline["value"])
+    r = run_batch(sub("batch256_fp32", steps=max(args.steps, 2)), WORKLOADS["batch256_fp32"])
+    extras["batch256_fp32"] = {
+        "value": r["value"], "unit": r["unit"], "ms_per_step": r["ms_per_step"],
+        "steps": r["steps"], "instances": r["config"]["instances"], "dof": r["config"]["dof"],
+        "sequential_ms_per_step": r["sequential_ms_per_step"],
+        "batched_speedup": r["batched_speedup"], "clocks": r["clocks"],
+        "device_error_flag": r["device_error_flag"], "workload": r["config"]["workload"]}
+    r = run_serve(sub("serve200_fp32"), WORKLOADS["serve200_fp32"])
+    extras["serve200_fp32"] = dict(r["serving"], value=r["value"], unit=r["unit"],
+                                   calibrated_capacity_dof_stage_per_s=
+                                   r["config"]["calibrated_capacity_dof_stage_per_s"],
+                                   arrival_rate_per_s=r["config"]["arrival_rate_per_s"],
+                                   clocks=r["clocks"], workload=r["config"]["workload"])
+    return extras
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -547,6 +632,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the float, batched and serving lines")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -573,6 +660,8 @@ def main():
         return run_reference(args, w)
     ws, rank, _ = _dist()
     out = run_native(args, w)
+    if ws == 1 and args.workload == DEFAULT and not args.no_extras:
+        out.update(run_extras(args, out))
     if rank == 0 and out is not None:
         if ws == 1 and not args.no_cpu_baseline:
             # bounded sample: one LSERK45 step of the full workload if it is

@@ -311,26 +311,31 @@ dg_status dg_batch_last_error(const dg_batch *batch);
  * allocates the handle's workspace.  This entry point evaluates the same
  * dQ/dt as dg_rhs for the mesh its arguments describe (the arguments mean what
  * they mean for dg_mesh_create) without allocating or freeing anything: the
- * 1D operators are computed on the host on every call, and the interface-
- * flux scratch lives in one static device array of DG_STATIC_SCRATCH_BYTES
- * (16 MiB) that every GPU which loads this library holds until the process
- * exits.  Q and R are caller-owned device states in the layout above, double
- * for DG_FP64 and float for DG_FP32; R must not overlap Q.
+ * 1D operators are computed on the host on every call.  Q and R are
+ * caller-owned device states in the layout above, double for DG_FP64 and
+ * float for DG_FP32, each exactly 5 * nx*ny*nz*(p+1)^3 scalars (the library
+ * cannot check their size: a smaller buffer is read or written out of
+ * bounds); R must not overlap Q.
  *
- * Size limit: the interface fluxes take 15 * nx*ny*nz*(p+1)^2 scalars; a
- * mesh that needs more than DG_STATIC_SCRATCH_BYTES is rejected with
- * DG_ERR_TOO_LARGE before anything is enqueued (e.g. p = 4 in double fits up
- * to 5,592 elements, 16^3 = 4,096 does; float doubles that).
- *
- * Set-up: the first call on each device looks up the device address of the
- * static array (cudaGetSymbolAddress, with that device current) and keeps
- * it; make that first call before any stream capture.
- *
- * Sharing: every call uses the same array, which keeps whatever the last call
- * left in it (each call writes the part it reads before reading it, so
- * nothing needs clearing).  Calls whose GPU work can overlap -- issued on
- * different streams, or from several host threads -- race on the array; the
- * caller must order them.
+ * DG_FP64 needs scratch for the interface fluxes: it lives in one static
+ * device array of DG_STATIC_SCRATCH_BYTES (16 MiB) that every GPU which
+ * loads this library holds until the process exits.
+ *   Size limit: 15 * nx*ny*nz*(p+1)^2 doubles; a mesh that needs more is
+ *   rejected with DG_ERR_TOO_LARGE before anything is enqueued (p = 4 fits
+ *   up to 5,592 elements, 16^3 = 4,096 does).
+ *   Set-up: the first DG_FP64 call on each device looks up the device
+ *   address of the static array (cudaGetSymbolAddress, with that device
+ *   current) and keeps it for the life of the process; make that first call
+ *   before any stream capture.  A device reset (cudaDeviceReset) between
+ *   calls is not supported: the kept address would no longer be valid.
+ *   Sharing: every DG_FP64 call uses the same array, which keeps whatever
+ *   the last call left in it (each call writes the part it reads before
+ *   reading it, so nothing needs clearing).  Calls whose GPU work can
+ *   overlap -- issued on different streams, or from several host threads --
+ *   race on the array; the caller must order them.
+ * DG_FP32 needs no scratch (its single-pass kernel keeps the interface
+ * fluxes in shared memory): no size limit beyond dg_mesh_create's, no set-up
+ * and no sharing between calls.
  *
  * Errors: DG_ERR_ARG / DG_ERR_UNSUPPORTED for the argument checks of
  * dg_mesh_create and dg_rhs, DG_ERR_TOO_LARGE as above, DG_ERR_CUDA if the
@@ -341,6 +346,16 @@ dg_status dg_rhs_static(int nx, int ny, int nz, int p,
                         double Lx, double Ly, double Lz,
                         double gamma, dg_precision precision,
                         const void *Q, void *R, void *stream);
+
+/* Measured multiply-add throughput of the current GPU's CUDA cores in
+ * flop/s (an FMA counts 2) at the given precision: independent FMA chains
+ * on every resident thread of the device, one untimed and one timed launch
+ * (about 20 ms; synchronises the device).  The roofline denominator of the
+ * double-state kernels, whose time goes to the FP64 pipe (the paper reports
+ * its kernels against the V100's peak flop rate, Sec. VI.B, Table II).  ms
+ * (nullable) receives the timed launch's duration.  Allocates and frees a
+ * few bytes of device memory.  Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
+dg_status dg_fma_throughput(dg_precision precision, double *flop_per_s, double *ms);
 
 /* Static text for a status code. */
 const char *dg_status_string(dg_status status);

@@ -16,7 +16,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libdg_gb300.so")
 SOURCES = ["dg_api.cu", "dg_kernels_f64.cu", "dg_kernels_f32.cu", "dg_batch_f32.cu",
            "dg_f32_deg01.cu", "dg_f32_deg2.cu", "dg_f32_deg3.cu", "dg_f32_deg4.cu",
-           "dg_f32_deg5.cu", "dg_f32_deg6.cu"]
+           "dg_f32_deg5.cu", "dg_f32_deg6.cu", "dg_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

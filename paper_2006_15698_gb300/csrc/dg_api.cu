@@ -396,9 +396,12 @@ dg_status dg_rhs_static(int nx, int ny, int nz, int p, double x0, double y0, dou
     const int N = p + 1;
     const long long E = (long long)nx * ny * nz;
     if (E * N * N * N >= (1LL << 40)) return DG_ERR_ARG;
-    const size_t esz = precision == DG_FP64 ? sizeof(double) : sizeof(float);
-    const double need = 3.0 * dg::NF * (double)E * N * N * (double)esz;
-    if (need > (double)DG_STATIC_SCRATCH_BYTES) return DG_ERR_TOO_LARGE;
+    // only the double form has interface-flux scratch (the float form's
+    // single-pass stage keeps its interface fluxes in shared memory)
+    if (precision == DG_FP64) {
+        const double need = 3.0 * dg::NF * (double)E * N * N * (double)sizeof(double);
+        if (need > (double)DG_STATIC_SCRATCH_BYTES) return DG_ERR_TOO_LARGE;
+    }
 
     dg::Geo g{};
     g.nx = nx; g.ny = ny; g.nz = nz; g.p = p; g.E = E;
@@ -416,9 +419,10 @@ dg_status dg_rhs_static(int nx, int ny, int nz, int p, double x0, double y0, dou
     const double gf[3] = {2.0 / g.hx, 2.0 / g.hy, 2.0 / g.hz};
 
     dg::Work w;
-    cudaError_t e = static_scratch_address(&w.face_flux);
-    if (e != cudaSuccess) return DG_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
     if (precision == DG_FP64) {
+        e = static_scratch_address(&w.face_flux);
+        if (e != cudaSuccess) return DG_ERR_CUDA;
         dg::Ops<double> ops;
         fill_ops(B, gf, ops);
         fill_gas(gamma, ops);

@@ -96,6 +96,23 @@ struct Work {
 
 constexpr int kNormBlocks = 1024;  // fixed partition of the norms reduction
 
+// Streaming multiprocessors of the current device (queried once per device;
+// a benign race: concurrent first calls store the same value).  Grid-stride
+// kernels size their grids as a multiple of it.
+inline int sm_count()
+{
+    constexpr int kDevices = 64;
+    static int cache[kDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev >= 0 && dev < kDevices && cache[dev] > 0) return cache[dev];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+        n = 1;
+    if (dev >= 0 && dev < kDevices) cache[dev] = n;
+    return n;
+}
+
 // Tile variant of the float form's fused stage per N = p + 1 (process-wide
 // tuning table, set through dg_set_tile_variant; read at each launch).
 int tile_variant(int N);

@@ -1116,7 +1116,7 @@ cudaError_t Launch<real>::cfl(const Geo &g, const real *Q, double cfl, double *d
     const int N = g.p + 1;
     const long long nodes = g.E * N * N * N;
     ProfScope ps(w.prof, kKindCfl, s);
-    cfl_kernel<real><<<grid_for(nodes, 256, 152 * 8), 256, 0, s>>>(Q, nodes, g.gamma, w.lam_bits,
+    cfl_kernel<real><<<grid_for(nodes, 256, 8LL * sm_count()), 256, 0, s>>>(Q, nodes, g.gamma, w.lam_bits,
                                                                     w.err);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
@@ -1146,7 +1146,7 @@ cudaError_t Launch<real>::init(const Geo &g, int kind, const double *params, rea
     const int N = g.p + 1;
     const long long nodes = g.E * N * N * N;
     ProfScope ps(w.prof, kKindInit, s);
-    init_kernel<real><<<grid_for(nodes, 256, 152 * 16), 256, 0, s>>>(g, kind, prm, Q);
+    init_kernel<real><<<grid_for(nodes, 256, 16LL * sm_count()), 256, 0, s>>>(g, kind, prm, Q);
     return cudaGetLastError();
 }
 

@@ -17,7 +17,7 @@ cudaError_t float_lambda(const Geo &g, const float *Q, unsigned long long *lam_b
                          cudaStream_t s)
 {
     const long long nodes = g.E * (long long)(g.p + 1) * (g.p + 1) * (g.p + 1);
-    cfl_kernel<float><<<grid_for(nodes, 256, 152 * 8), 256, 0, s>>>(Q, nodes, g.gamma, lam_bits,
+    cfl_kernel<float><<<grid_for(nodes, 256, 8LL * sm_count()), 256, 0, s>>>(Q, nodes, g.gamma, lam_bits,
                                                                      err);
     return cudaGetLastError();
 }

@@ -113,6 +113,20 @@ _lib.dg_batch_norms.restype = ctypes.c_int
 _lib.dg_batch_last_error.argtypes = [_vp]
 _lib.dg_batch_last_error.restype = ctypes.c_int
 
+_lib.dg_fma_throughput.argtypes = [ctypes.c_int, _dp, _dp]
+_lib.dg_fma_throughput.restype = ctypes.c_int
+
+
+def dg_fma_throughput(precision):
+    """(flop/s, ms of the timed launch) of independent FMA chains on the
+    current device at the given precision (the roofline denominator of the
+    arithmetic-bound kernels)."""
+    f, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.dg_fma_throughput(precision, ctypes.byref(f), ctypes.byref(ms)),
+           "dg_fma_throughput")
+    return f.value, ms.value
+
+
 DG_PROFILE_KINDS = 8
 KERNEL_KINDS = ("face", "volume", "cfl", "norms", "init", "stage", "copy", "epilogue")
 DG_ERR_TOO_LARGE = 8
@@ -197,9 +211,29 @@ def dg_last_error(h):
 
 
 def dg_rhs_static(nx, ny, nz, p, x0, y0, z0, Lx, Ly, Lz, gamma, precision, Q, R, stream=None):
-    """Allocation-free right-hand side (no mesh handle; scratch in a static
-    device array, see include/dg.h).  For callers that cannot let a library
-    allocate device memory."""
+    """Allocation-free right-hand side (no mesh handle; the double form's
+    scratch is a static device array, see include/dg.h).  For callers that
+    cannot let a library allocate device memory.
+
+    The C function cannot see the size of Q and R, so they are checked here
+    before the call: torch tensors on the current CUDA device, contiguous, of
+    the precision's dtype and exactly 5 nx ny nz (p+1)^3 elements (when the
+    mesh arguments are in range; otherwise the library rejects them)."""
+    dtype = {DG_FP64: torch.float64, DG_FP32: torch.float32}.get(precision)
+    for name, t in (("Q", Q), ("R", R)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"dg_rhs_static: {name} must be a torch tensor")
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise ValueError(f"dg_rhs_static: {name} must be on the current CUDA device")
+        if not t.is_contiguous():
+            raise ValueError(f"dg_rhs_static: {name} must be contiguous")
+        if dtype is not None and t.dtype != dtype:
+            raise ValueError(f"dg_rhs_static: {name} must be {dtype} for this precision")
+        if min(nx, ny, nz) >= 1 and 0 <= p <= DG_MAX_P:
+            need = NF * nx * ny * nz * (p + 1) ** 3
+            if t.numel() != need:
+                raise ValueError(f"dg_rhs_static: {name} has {t.numel()} elements, "
+                                 f"the mesh needs {need}")
     _check(_lib.dg_rhs_static(nx, ny, nz, p, x0, y0, z0, Lx, Ly, Lz, gamma, precision,
                               _ptr(Q), _ptr(R), _stream(stream)), "dg_rhs_static")
 

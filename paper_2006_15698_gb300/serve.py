@@ -187,7 +187,12 @@ class Server:
 
 
 class GpuExecutor:
-    """Runs the batch on the current CUDA device through the C library."""
+    """Runs the batch on the current CUDA device through the C library.
+
+    The library steps a batch with one CFL number, so the active requests are
+    grouped by their CFL number into one batch per distinct value, stepped
+    one after the other on the executor's stream: every request takes its
+    own time steps, whatever else is active."""
 
     def __init__(self, stream=None):
         import torch
@@ -195,9 +200,9 @@ class GpuExecutor:
         from . import dg
         self.torch, self.dg = torch, dg
         self.stream = stream or torch.cuda.Stream()
-        self.handles = {}     # rid -> dict(Q, dQ, Qt, fresh)
-        self.batch = None
-        self.order = []
+        self.handles = {}     # rid -> dict(Q, dQ, Qt, fresh, req)
+        self.groups = []      # [(cfl, Batch, [rid, ...])]
+        self.where = {}       # rid -> (group index, index in the batch)
         self.event = None
 
     def admit(self, q):
@@ -210,26 +215,33 @@ class GpuExecutor:
         self.handles[q.rid] = h
 
     def rebuild(self, reqs):
-        specs = []
+        by_cfl = {}
         for q in reqs:
-            h = self.handles[q.rid]
-            s = q.spec()
-            s.update(Q=h["Q"], dQ=h["dQ"], Qt=h["Qt"])
-            specs.append(s)
-        self.order = [q.rid for q in reqs]
+            by_cfl.setdefault(float(q.cfl), []).append(q)
         with self.torch.cuda.stream(self.stream):
-            self.batch = None
-            self.batch = self.dg.Batch(specs)
-            for idx, q in enumerate(reqs):
-                h = self.handles[q.rid]
-                if h["fresh"]:
-                    self.batch.init(idx, q.kind, q.params)
-                    h["fresh"] = False
+            self.groups = []
+            self.where = {}
+            for cfl in sorted(by_cfl):
+                members = by_cfl[cfl]
+                specs = []
+                for q in members:
+                    h = self.handles[q.rid]
+                    s = q.spec()
+                    s.update(Q=h["Q"], dQ=h["dQ"], Qt=h["Qt"])
+                    specs.append(s)
+                batch = self.dg.Batch(specs)
+                for idx, q in enumerate(members):
+                    h = self.handles[q.rid]
+                    if h["fresh"]:
+                        batch.init(idx, q.kind, q.params)
+                        h["fresh"] = False
+                    self.where[q.rid] = (len(self.groups), idx)
+                self.groups.append((cfl, batch, [q.rid for q in members]))
 
     def step(self, k):
-        cfl = self.handles[self.order[0]]["req"].cfl
         with self.torch.cuda.stream(self.stream):
-            self.batch.step(cfl, nsteps=k, use_graph=True)
+            for cfl, batch, _ in self.groups:
+                batch.step(cfl, nsteps=k, use_graph=True)
             self.event = self.torch.cuda.Event()
             self.event.record(self.stream)
 
@@ -244,9 +256,9 @@ class GpuExecutor:
 
     def finish(self, q, keep_state=False):
         h = self.handles.pop(q.rid)
-        idx = self.order.index(q.rid)
+        g, idx = self.where[q.rid]
         with self.torch.cuda.stream(self.stream):
-            integrals = self.batch.norms(idx).cpu().tolist()
+            integrals = self.groups[g][1].norms(idx).cpu().tolist()
             state = h["Q"].cpu() if keep_state else None
         return {"integrals": integrals, "state": state}
 

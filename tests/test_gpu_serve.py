@@ -26,3 +26,30 @@ def test_alone_equals_in_the_mix():
         m = mix.outcomes[q.rid].result
         assert torch.equal(a["state"], m["state"]), q
         assert a["integrals"] == m["integrals"]
+
+
+def test_mixed_cfl_alone_equals_in_the_mix():
+    # requests with different CFL numbers share the device: each takes its own
+    # time steps (one batch per CFL number), so its result is the one it gets
+    # alone, bit for bit
+    dg_module()
+    import torch
+    reqs = serve.make_requests(9, 8, 500.0, nrange=(3, 6), prange=(1, 4), steps_range=(3, 6),
+                               L=10.0)
+    for i, q in enumerate(reqs):
+        q.cfl = (0.3, 0.5, 0.8)[i % 3]
+    budget = 8 * max(q.device_bytes() for q in reqs)
+    mix = serve.Server(serve.GpuExecutor(), budget, keep_states=True).run(reqs)
+    assert len(mix.outcomes) == len(reqs) and mix.peak_active >= 3
+    for q in reqs:
+        alone = serve.Server(serve.GpuExecutor(), budget, keep_states=True).run(
+            [serve.Request(q.rid, 0.0, q.n, q.p, q.kind, q.nsteps, q.L, q.cfl, q.params)])
+        a = alone.outcomes[0].result
+        m = mix.outcomes[q.rid].result
+        assert torch.equal(a["state"], m["state"]), q
+        assert a["integrals"] == m["integrals"]
+    # the CFL number matters: the same request at another CFL ends elsewhere
+    q = reqs[0]
+    other = serve.Server(serve.GpuExecutor(), budget, keep_states=True).run(
+        [serve.Request(q.rid, 0.0, q.n, q.p, q.kind, q.nsteps, q.L, 0.45, q.params)])
+    assert not torch.equal(other.outcomes[0].result["state"], mix.outcomes[q.rid].result["state"])
