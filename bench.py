@@ -10,8 +10,15 @@ quadrature integrals of the new state.  value = DOF x 5 stages x steps x ranks
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 
-Multi-GPU: one process per GPU (torchrun), each rank an independent replica
-of the workload (the path has no data exchange on one box): weak scaling.
+The default run (one GPU) also measures, in the same process, the FP32 bulk
+form (128^3 p=3, and the headline's 64^3 p=4 for the FP32/FP64 ratio), the
+batched form (256 uneven instances) and the serving loop (200 requests):
+extra keys of the JSON line (--no-extras skips them).
+
+Multi-GPU: one process per GPU (torchrun).  By default the workload's mesh is
+split along z into one slab per rank, the slabs exchanging face traces every
+RK stage over NCCL (strong scaling); --replicas runs independent replicas
+instead (weak scaling).
 """
 import argparse
 import hashlib
@@ -51,6 +58,9 @@ WORKLOADS = {
     "vortex64_p3_fp32": dict(nel=(64, 64, 64), p=3, box=(0, 0, 0, 16.0, 16.0, 16.0),
                              init="vortex", params=None, prec="fp32", cfl=0.5,
                              desc="isentropic vortex (seed 0), 16^3 box, 64^3 elements, p=3, FP32"),
+    "vortex48_p4_fp32": dict(nel=(48, 48, 48), p=4, box=(0, 0, 0, 16.0, 16.0, 16.0),
+                             init="vortex", params=None, prec="fp32", cfl=0.5,
+                             desc="isentropic vortex (seed 0), 16^3 box, 48^3 elements, p=4, FP32"),
     "vortex8_p3_fp64": dict(nel=(8, 8, 8), p=3, box=(0, 0, 0, 10.0, 10.0, 10.0),
                             init="vortex", params=None, prec="fp64", cfl=0.5,
                             desc="isentropic vortex (seed 0), [0,10]^3, 8^3 elements, p=3, FP64"),
@@ -428,8 +438,9 @@ def run_reference(args, w):
     dof = nel[0] * nel[1] * nel[2] * (w["p"] + 1) ** 3
     out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": _config(w, args.workload, ws),
+           "higher_is_better": True, "scaling": "strong" if _sharded(args, ws) else "weak",
+           "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": _config(w, args.workload, ws, _parallelism(args, ws)),
            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"{args.steps} LSERK45 steps (CFL + 5 stages + integrals) of "
                                       f"the same problem on a {nel[0]}x{nel[1]}x{nel[2]}-element "
@@ -439,7 +450,17 @@ def run_reference(args, w):
     return 0
 
 
-def _config(w, name, ws=1):
+def _sharded(args, ws):
+    return (ws > 1 and not getattr(args, "replicas", False)) or getattr(args, "sharded", False)
+
+
+def _parallelism(args, ws):
+    if _sharded(args, ws):
+        return f"z slabs x{ws} (one per GPU, NCCL face-trace exchange per stage)"
+    return f"replicas x{ws}"
+
+
+def _config(w, name, ws=1, parallelism=None):
     """The workload's configuration, the same dict in both arms."""
     nx, ny, nz = w["nel"]
     N = w["p"] + 1
@@ -448,7 +469,7 @@ def _config(w, name, ws=1):
     return {"workload": f"{name}: {w['desc']}; one step = CFL reduction + LSERK45 step + integrals",
             "elements": nx * ny * nz, "p": w["p"], "dof": dof,
             "unknowns": 5 * dof, "cfl": w["cfl"], "precision": w["prec"],
-            "parallelism": f"replicas x{ws}",
+            "parallelism": parallelism or f"replicas x{ws}",
             "l2": f"state arrays {state_gb:.2f} GB each, larger than the 129 MB L2"}
 
 
@@ -624,6 +645,116 @@ def run_extras(args, headline):
     return extras
 
 
+def run_sharded(args, w):
+    """N > 1 ranks, one GPU each: the workload's single mesh split along z
+    into N slabs (one per rank) that exchange face traces every RK stage
+    (NCCL point-to-point) and reduce the time step (MIN) and the integrals
+    (SUM) -- the paper's partitioned mesh (Sec. III, IV).  Strong scaling:
+    value = the whole mesh's DOF x 5 stages x steps / the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    from paper_2006_15698_gb300 import dg, slabs
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    nx, ny, nz = w["nel"]
+    N = w["p"] + 1
+    prec = dg.DG_FP64 if w["prec"] == "fp64" else dg.DG_FP32
+    esz = 8 if prec == dg.DG_FP64 else 4
+    zb, nzs = slabs.split_layers(nz, ws)[rank]
+    box = slabs.slab_box(w["box"], nz, zb, nzs)
+    slab = slabs.GpuSlab((nx, ny, nzs), w["p"], box, prec)
+    slab.mesh.init(w["init"], _params(w), Q=slab.Q)
+    solver = slabs.SlabSolver([slab])
+    stream = torch.cuda.current_stream()
+    integ = torch.zeros(6, dtype=torch.float64, device="cuda")
+
+    def steps(n):
+        for _ in range(n):
+            solver.step(w["cfl"])
+            integ.copy_(solver.integrals())
+
+    steps(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.25)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    slab.mesh.profile_begin()
+    torch.cuda.synchronize()
+    barrier()
+    ev0.record(stream)
+    steps(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = slab.mesh.profile_end()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    ck = clocks.stop()
+    err = slab.mesh.last_error()
+    dof_all = nx * ny * nz * N ** 3
+    value, ms_max = whole_job_rate(ms, dof_all * 5 * args.steps / ws, device="cuda")
+
+    # end to end: each rank's slab state from pinned host memory and back, per step
+    e2e_steps = max(1, min(args.steps, 10))
+    Qh = torch.empty(slab.Q.shape, dtype=slab.Q.dtype, pin_memory=True)
+    Qh.copy_(slab.Q)
+    integ_h = torch.empty(6, dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        slab.Q.copy_(Qh, non_blocking=True)
+        steps(1)
+        Qh.copy_(slab.Q, non_blocking=True)
+        integ_h.copy_(integ, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_val, _ = whole_job_rate(e0.elapsed_time(e1), dof_all * 5 * e2e_steps / ws, device="cuda")
+    out = None
+    if rank == 0:
+        E = nx * ny * nzs
+        dom = max((k for k in ("face", "volume", "stage") if prof[k][1]), key=lambda k: prof[k][0])
+        avg_s = prof[dom][0] / prof[dom][1] / 1e3
+        peaks, src = _peaks()
+        if prec == dg.DG_FP64:
+            ach = kernel_flops(dom, N, E) / avg_s / 1e12
+            pk = fp64_peak(dg)
+            roof = {"bound": "alu", "achieved": ach, "peak": pk["peak"], "unit": "TFLOP/s",
+                    "frac": ach / pk["peak"], "peak_source": pk["source"], "kernel": dom}
+        else:
+            gbs = kernel_bytes(dom, N, E, esz) / avg_s / 1e9
+            roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": gbs / peaks["hbm_gbs"], "peak_source": src, "kernel": dom}
+        roof["traffic"] = None
+        n_st = prof["face"][1] + prof["volume"][1] + prof["stage"][1]
+        launches = n_st + 2 * prof["cfl"][1] + 2 * prof["norms"][1] + 5 * args.steps  # + ztraces
+        cfg = _config(w, args.workload, ws, _parallelism(args, ws))
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "strong", "vs_baseline": None,
+               "dtype": "f64" if prec == dg.DG_FP64 else "f32", "data": "synthetic",
+               "config": cfg, "roofline": roof, "gpu_launches": launches,
+               "e2e": {"value": e2e_val, "unit": UNIT, "steps": e2e_steps,
+                       "h2d_bytes_per_step": slab.mesh.state_bytes,
+                       "d2h_bytes_per_step": slab.mesh.state_bytes + 8 * 6},
+               "clocks": ck, "device_error_flag": err}
+    barrier()
+    if ws > 1:
+        dist.destroy_process_group()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -632,6 +763,11 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--replicas", action="store_true",
+                    help="N > 1: independent replicas of the workload instead of one mesh split "
+                         "into N z slabs")
+    ap.add_argument("--sharded", action="store_true",
+                    help="the z-slab path even on one GPU (one slab, halos from itself)")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload only: skip the float, batched and serving lines")
     args = ap.parse_args()
@@ -659,6 +795,11 @@ def main():
     if args.impl == "reference":
         return run_reference(args, w)
     ws, rank, _ = _dist()
+    if _sharded(args, ws):
+        out = run_sharded(args, w)
+        if rank == 0 and out is not None:
+            print(json.dumps(out))
+        return 0
     out = run_native(args, w)
     if ws == 1 and args.workload == DEFAULT and not args.no_extras:
         out.update(run_extras(args, out))

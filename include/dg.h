@@ -152,6 +152,58 @@ dg_status dg_cfl_dt(const dg_mesh *mesh, const void *Q, double cfl, double *dt_d
 dg_status dg_rk_step(const dg_mesh *mesh, void *Q, void *dQ, const double *dt_dev,
                      void *stream);
 
+/* One stage of dg_rk_step's scheme (stage = 0..4, A_1 = 0):
+ *     dQ <- A_s dQ + dt * dQ/dt(Qin),   Qout <- Qin + B_s dQ
+ * with the right-hand side of the whole mesh at Qin.  Five calls with
+ * stages 0..4 are one LSERK45 step (for DG_FP64 with Qin == Qout they equal
+ * dg_rk_step bit for bit; for DG_FP32 Qout must be another state buffer,
+ * because neighbouring elements still read Qin while the stage writes, and
+ * the stages alternate between two states).  The stage-by-stage form is what
+ * a z slab (below) needs: its halo traces change between stages.  Errors:
+ * DG_ERR_ARG (NULL, stage out of range, dQ equal to Qin or Qout, Qin == Qout
+ * for DG_FP32, unaligned states), DG_ERR_UNSUPPORTED (a DG_FP32 slab whose
+ * degree runs the tile stage kernel). */
+dg_status dg_rk_stage(const dg_mesh *mesh, const void *Qin, void *Qout, void *dQ,
+                      const double *dt_dev, int stage, void *stream);
+
+/* z slabs: one periodic mesh partitioned across GPUs (Sec. III and Sec. IV:
+ * the paper splits its mesh over MPI ranks, each GPU holding a partition, and
+ * neighbouring partitions exchange element face data every stage).
+ *
+ * A slab is a dg_mesh of nz layers of a taller box that is periodic in x and
+ * y (create it with the slab's own z0 and Lz = nz * hz, hz the element size
+ * of the whole box).  dg_mesh_set_zhalo makes its z boundary an interface to
+ * other slabs instead of the periodic wrap: the -z neighbour of layer 0 and
+ * the +z neighbour of layer nz-1 are then known only through their face
+ * traces, read from two caller-owned DEVICE buffers of the state's scalar
+ * type, each 5 * nx*ny * N^2 values in the layout H[field][ey*nx + ex][j*N + i]
+ * (face point (i, j) of the element column (ex, ey)):
+ *     halo_lo  the +z-end traces of the layer below layer 0
+ *     halo_hi  the -z-end traces of the layer above layer nz-1.
+ * The handle keeps the pointers (not the contents): every later dg_rhs and
+ * dg_rk_stage reads the buffers as they are when its kernels run.  Passing
+ * two NULLs restores the periodic wrap.  For DG_FP64 the first call
+ * allocates the handle's buffer for the -z interface fluxes of layer 0
+ * (5 * nx*ny * N^2 doubles).  dg_rk_step and dg_advance return
+ * DG_ERR_UNSUPPORTED while halos are set (their stages would need new halos
+ * in between); dg_cfl_dt and dg_norms are local and unchanged.
+ *
+ * dg_zhalo_traces writes what the slab's neighbours need, in the same
+ * layout: send_lo = layer 0's traces at its -z end (the halo_hi of the slab
+ * below), send_hi = layer nz-1's traces at its +z end (the halo_lo of the
+ * slab above).  The traces are computed with the same arithmetic as the
+ * stage kernels' own, so a mesh split into slabs whose halos are filled from
+ * their neighbours' dg_zhalo_traces before every stage evolves bit for bit
+ * as the undivided mesh (time steps: the minimum of the slabs' dg_cfl_dt,
+ * which equals the undivided mesh's; integrals: the sums of the slabs').
+ *
+ * Errors: DG_ERR_ARG (NULL mesh or state, one halo NULL and the other not,
+ * send_lo == send_hi), DG_ERR_UNSUPPORTED (a DG_FP32 mesh whose degree runs
+ * the tile stage kernel), DG_ERR_OOM. */
+dg_status dg_mesh_set_zhalo(dg_mesh *mesh, const void *halo_lo, const void *halo_hi);
+dg_status dg_zhalo_traces(const dg_mesh *mesh, const void *Q, void *send_lo, void *send_hi,
+                          void *stream);
+
 /* Quadrature integrals of the state with the collocated rule (weight
  * J w_i w_j w_k per node, J = hx hy hz / 8), accumulated in double in a fixed
  * order (the result is bitwise reproducible for a given mesh):
@@ -356,6 +408,22 @@ dg_status dg_rhs_static(int nx, int ny, int nz, int p,
  * (nullable) receives the timed launch's duration.  Allocates and frees a
  * few bytes of device memory.  Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_fma_throughput(dg_precision precision, double *flop_per_s, double *ms);
+
+/* Measured FP64 tensor-core (DMMA) throughput of the current GPU in flop/s:
+ * independent accumulators through mma.sync m8n8k4 f64 (512 flop per warp
+ * instruction) on every resident warp; with mix = 1 the odd warps run FP64
+ * FMA chains of the same flop count instead, which shows whether the two
+ * kinds of FP64 work share one pipe.  Answers whether the sum-factorised
+ * contractions (N x N matrices, N <= 7) could move to tensor cores.  Same
+ * conventions as dg_fma_throughput. */
+dg_status dg_dmma_throughput(int mix, double *flop_per_s, double *ms);
+
+/* Self-check of the double form's sound-speed square root (a refined
+ * reciprocal-square-root approximation, not the correctly rounded sqrt):
+ * for n positive doubles a (DEVICE), writes the kernels' root to fast[] and
+ * CUDA's correctly rounded __dsqrt_rn to ieee[] (both DEVICE, n doubles),
+ * asynchronously on stream.  Lets a test bound the difference in ulp. */
+dg_status dg_selfcheck_sqrt(const double *a, double *fast, double *ieee, int64_t n, void *stream);
 
 /* Static text for a status code. */
 const char *dg_status_string(dg_status status);

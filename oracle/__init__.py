@@ -66,6 +66,9 @@ def _bind(lib):
     lib.dgo_cfl_dt.restype = ctypes.c_double
     lib.dgo_norms.argtypes = [M, _DP, _DP, _DP]
     lib.dgo_state_init.argtypes = [M, ctypes.c_int, _DP, ctypes.c_int, _DP]
+    lib.dgo_ztraces.argtypes = [M, _DP, _DP, _DP]
+    lib.dgo_rhs_o2_zhalo.argtypes = [M, _DP, _DP, _DP, _DP]
+    lib.dgo_rk_stage.argtypes = [M, _DP, _DP, ctypes.c_double, ctypes.c_int, _DP, _DP]
     lib.dgo_num_threads.restype = ctypes.c_int
     lib.dgo_set_num_threads.argtypes = [ctypes.c_int]
     lib.dgo_set_num_threads.restype = None
@@ -145,6 +148,41 @@ class Mesh:
         if st:
             raise RuntimeError("oracle norms failed")
         return out
+
+    # --- z slabs: the mesh is one slab of a taller box; its z neighbours
+    # beyond its own layers enter through halo traces [5][ny*nx][N*N]
+
+    @property
+    def halo_shape(self):
+        return (NF, self.nx * self.ny, self.N * self.N)
+
+    def ztraces(self, Q):
+        """(lo, hi): the traces of layer 0 at its -z end and of the last layer
+        at its +z end, in the halo layout."""
+        Q = _f64(Q)
+        lo, hi = np.empty(self.halo_shape), np.empty(self.halo_shape)
+        if self.lib.dgo_ztraces(ctypes.byref(self._m), _ptr(Q), _ptr(lo), _ptr(hi)):
+            raise RuntimeError("oracle ztraces failed")
+        return lo, hi
+
+    def rhs_zhalo(self, Q, halo_lo, halo_hi):
+        """O2 right-hand side with the z neighbours' traces taken from the halos."""
+        Q = _f64(Q)
+        R = np.empty_like(Q)
+        lo, hi = _f64(halo_lo), _f64(halo_hi)
+        if self.lib.dgo_rhs_o2_zhalo(ctypes.byref(self._m), _ptr(Q), _ptr(lo), _ptr(hi), _ptr(R)):
+            raise RuntimeError("oracle rhs_zhalo failed")
+        return R
+
+    def rk_stage(self, Q, dQ, dt, stage, halo_lo=None, halo_hi=None):
+        """LSERK45 stage `stage` (0..4) in place on the float64 arrays Q, dQ."""
+        assert Q.dtype == np.float64 and dQ.dtype == np.float64
+        assert Q.flags.c_contiguous and dQ.flags.c_contiguous
+        lo = None if halo_lo is None else _ptr(_f64(halo_lo))
+        hi = None if halo_hi is None else _ptr(_f64(halo_hi))
+        if self.lib.dgo_rk_stage(ctypes.byref(self._m), _ptr(Q), _ptr(dQ), float(dt), int(stage),
+                                 lo, hi):
+            raise RuntimeError("oracle rk_stage failed")
 
     def init(self, kind, params):
         kinds = {"uniform": 0, "vortex": 1, "tgv": 2}

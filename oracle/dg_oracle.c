@@ -251,6 +251,17 @@ static void collocated_trace(const dgo_mesh *m, const basis1d *b, const double *
     }
 }
 
+/* A z-face trace held in a halo buffer H[f][ey*nx + ex][t2*N + t1] (the
+ * layout of dgo_ztraces below). */
+static void halo_trace(const dgo_mesh *m, const double *H, int ex, int ey, int t1, int t2,
+                       double q[NF])
+{
+    const int N = m->p + 1;
+    const size_t plane = (size_t)m->nx * (size_t)m->ny;
+    const size_t col = (size_t)ey * (size_t)m->nx + (size_t)ex;
+    for (int f = 0; f < NF; ++f) q[f] = H[((size_t)f * plane + col) * (size_t)(N * N) + (size_t)(t2 * N + t1)];
+}
+
 /* ------------------------------------------------------------------------ */
 /* O2: collocated right-hand side, plain loops (Eq. 5 with psi(xi_abc) = delta) */
 /* ------------------------------------------------------------------------ */
@@ -269,8 +280,10 @@ static void collocated_trace(const dgo_mesh *m, const basis1d *b, const double *
  * F*x(-face) the flux through its -x face (left state: the -x neighbour).
  * The outward normal on the -x face is -x, hence the sign of that term. */
 /* O2 for one element e: out[n * N^3 + node] = R of field n at node (i,j,k). */
+/* halo_lo / halo_hi (NULL: periodic in z) replace the traces of the -z
+ * neighbour of layer 0 and of the +z neighbour of layer nz-1 (z slabs, below). */
 static void rhs_o2_element(const dgo_mesh *m, const basis1d *bp, const double *Q, int64_t e,
-                           double *out)
+                           const double *halo_lo, const double *halo_hi, double *out)
 {
     const basis1d b = *bp;
     const int N = m->p + 1;
@@ -304,12 +317,18 @@ static void rhs_o2_element(const dgo_mesh *m, const basis1d *bp, const double *Q
             for (int t1 = 0; t1 < N; ++t1) {
                 double qL[NF], qR[NF];
                 /* -face: left = -neighbour at its +1 end, right = this at -1 */
-                collocated_trace(m, &b, Q, em, d, +1, t1, t2, qL);
+                if (d == 2 && halo_lo && ez == 0)
+                    halo_trace(m, halo_lo, ex, ey, t1, t2, qL);
+                else
+                    collocated_trace(m, &b, Q, em, d, +1, t1, t2, qL);
                 collocated_trace(m, &b, Q, e, d, -1, t1, t2, qR);
                 dgo_lf_flux(d, qL, qR, gam, fhat[d][0][t2 * N + t1]);
                 /* +face: left = this at +1, right = +neighbour at -1 */
                 collocated_trace(m, &b, Q, e, d, +1, t1, t2, qL);
-                collocated_trace(m, &b, Q, ep, d, -1, t1, t2, qR);
+                if (d == 2 && halo_hi && ez == m->nz - 1)
+                    halo_trace(m, halo_hi, ex, ey, t1, t2, qR);
+                else
+                    collocated_trace(m, &b, Q, ep, d, -1, t1, t2, qR);
                 dgo_lf_flux(d, qL, qR, gam, fhat[d][1][t2 * N + t1]);
             }
     }
@@ -370,7 +389,7 @@ int dgo_rhs_o2(const dgo_mesh *m, const double *Q, double *R)
 #pragma omp parallel for schedule(static)
     for (int64_t e = 0; e < E; ++e) {
         double out[NF * NMAX * NMAX * NMAX];
-        rhs_o2_element(m, &b, Q, e, out);
+        rhs_o2_element(m, &b, Q, e, NULL, NULL, out);
         for (int n = 0; n < NF; ++n)
             for (int t = 0; t < N3; ++t) R[qidx(m, n, e, 0, 0, 0) + t] = out[n * N3 + t];
     }
@@ -393,7 +412,7 @@ int dgo_rhs_o2_elements(const dgo_mesh *m, const double *Q, int64_t nsel, const 
 #pragma omp parallel for schedule(static)
     for (int64_t s = 0; s < nsel; ++s) {
         double out[NF * NMAX * NMAX * NMAX];
-        rhs_o2_element(m, &b, Q, elems[s], out);
+        rhs_o2_element(m, &b, Q, elems[s], NULL, NULL, out);
         for (int n = 0; n < NF; ++n)
             for (int t = 0; t < N3; ++t) R[((size_t)n * nsel + s) * N3 + t] = out[n * N3 + t];
     }
@@ -648,16 +667,22 @@ typedef int (*dgo_rhs_fn)(void *ctx, const double *y, double *dydt);
 /* One step of the 2N-storage scheme on y (length n), work array k (length n):
  * for s = 1..5:  k <- A_s k + dt f(y);  y <- y + B_s k.
  * A_1 = 0, so k's incoming contents are never read. */
+/* stage s's update of the registers from f = dy/dt at the stage's start */
+static void lserk_update(int64_t n, double *y, double *k, const double *f, double dt, int s)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        k[i] = (s == 0 ? 0.0 : rk4a[s] * k[i]) + dt * f[i];
+        y[i] = y[i] + rk4b[s] * k[i];
+    }
+}
+
 static int lserk_step(int64_t n, double *y, double *k, double *f, double dt,
                       dgo_rhs_fn rhs, void *ctx)
 {
     for (int s = 0; s < 5; ++s) {
         int st = rhs(ctx, y, f);
         if (st) return st;
-        for (int64_t i = 0; i < n; ++i) {
-            k[i] = (s == 0 ? 0.0 : rk4a[s] * k[i]) + dt * f[i];
-            y[i] = y[i] + rk4b[s] * k[i];
-        }
+        lserk_update(n, y, k, f, dt, s);
     }
     return 0;
 }
@@ -712,6 +737,79 @@ int dgo_rk_steps(const dgo_mesh *m, double *Q, double *dQ, double dt, int nsteps
     int st = 0;
     for (int s = 0; s < nsteps && st == 0; ++s)
         st = lserk_step((int64_t)n, Q, dQ, f, dt, dg_rhs_cb, &c);
+    free(f);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* z slabs (Sec. III, Sec. IV: the mesh is partitioned and neighbouring      */
+/* partitions exchange element face data every stage).  A slab is a mesh of  */
+/* nz layers of a taller periodic box; its z neighbours beyond its own       */
+/* layers belong to other slabs and enter only through their face traces.    */
+/* ------------------------------------------------------------------------ */
+
+/* The face traces a slab sends to its z neighbours, in the halo layout
+ * H[f][ey*nx + ex][j*N + i]:
+ *   lo = the traces of layer 0 at its -z end (the slab below needs them as
+ *        its halo_hi),
+ *   hi = the traces of layer nz-1 at its +z end (the slab above needs them
+ *        as its halo_lo). */
+int dgo_ztraces(const dgo_mesh *m, const double *Q, double *lo, double *hi)
+{
+    if (!mesh_ok(m) || !Q || !lo || !hi) return 1;
+    const int N = m->p + 1;
+    basis1d b;
+    make_basis(N, &b);
+    const size_t plane = (size_t)m->nx * (size_t)m->ny;
+    for (size_t col = 0; col < plane; ++col)
+        for (int j = 0; j < N; ++j)
+            for (int i = 0; i < N; ++i) {
+                double ql[NF], qh[NF];
+                collocated_trace(m, &b, Q, (int64_t)col, 2, -1, i, j, ql);
+                collocated_trace(m, &b, Q, (int64_t)(col + (size_t)(m->nz - 1) * plane), 2, +1,
+                                 i, j, qh);
+                for (int f = 0; f < NF; ++f) {
+                    lo[((size_t)f * plane + col) * (size_t)(N * N) + (size_t)(j * N + i)] = ql[f];
+                    hi[((size_t)f * plane + col) * (size_t)(N * N) + (size_t)(j * N + i)] = qh[f];
+                }
+            }
+    return 0;
+}
+
+/* O2 right-hand side of a slab: the trace of the -z neighbour of layer 0
+ * is read from halo_lo, that of the +z neighbour of layer nz-1 from halo_hi
+ * (layout of dgo_ztraces; both NULL: periodic in z, as dgo_rhs_o2). */
+int dgo_rhs_o2_zhalo(const dgo_mesh *m, const double *Q, const double *halo_lo,
+                     const double *halo_hi, double *R)
+{
+    if (!mesh_ok(m) || !Q || !R || (!halo_lo) != (!halo_hi)) return 1;
+    const int N = m->p + 1;
+    const int N3 = N * N * N;
+    basis1d b;
+    make_basis(N, &b);
+    const int64_t E = n_elem(m);
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < E; ++e) {
+        double out[NF * NMAX * NMAX * NMAX];
+        rhs_o2_element(m, &b, Q, e, halo_lo, halo_hi, out);
+        for (int n = 0; n < NF; ++n)
+            for (int t = 0; t < N3; ++t) R[qidx(m, n, e, 0, 0, 0) + t] = out[n * N3 + t];
+    }
+    return 0;
+}
+
+/* Stage s (0..4) of the LSERK45 step of a slab, in place:
+ * dQ <- A_s dQ + dt R(Q), Q <- Q + B_s dQ, with R from dgo_rhs_o2_zhalo
+ * (five stages with periodic z are one dgo_rk_steps step). */
+int dgo_rk_stage(const dgo_mesh *m, double *Q, double *dQ, double dt, int s,
+                 const double *halo_lo, const double *halo_hi)
+{
+    if (!mesh_ok(m) || !Q || !dQ || s < 0 || s > 4) return 1;
+    size_t n = state_len(m);
+    double *f = (double *)malloc(sizeof(double) * n);
+    if (!f) return 2;
+    int st = dgo_rhs_o2_zhalo(m, Q, halo_lo, halo_hi, f);
+    if (st == 0) lserk_update((int64_t)n, Q, dQ, f, dt, s);
     free(f);
     return st;
 }

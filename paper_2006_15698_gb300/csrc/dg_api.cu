@@ -148,6 +148,7 @@ dg_status cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess) return DG_OK;
     if (e == cudaErrorMemoryAllocation) return DG_ERR_OOM;
+    if (e == cudaErrorNotSupported) return DG_ERR_UNSUPPORTED;  // a launcher's own refusal
     return DG_ERR_CUDA;
 }
 
@@ -238,6 +239,7 @@ void dg_mesh_destroy(dg_mesh *m)
     cudaDeviceSynchronize();
     cudaFree(m->work.face_flux);
     cudaFree(m->work.qtmp);
+    cudaFree(m->work.zflux);
     cudaFree(m->work.partials);
     cudaFree(m->work.lam_bits);
     cudaFree(m->work.err);
@@ -308,6 +310,7 @@ dg_status dg_cfl_dt(const dg_mesh *m, const void *Q, double cfl, double *dt_dev,
 dg_status dg_rk_step(const dg_mesh *m, void *Q, void *dQ, const double *dt_dev, void *stream)
 {
     if (!m || !Q || !dQ || !dt_dev || Q == dQ || !aligned16(Q) || !aligned16(dQ)) return DG_ERR_ARG;
+    if (m->geo.zlo) return DG_ERR_UNSUPPORTED;  // a slab's halos change between stages
     dg::Work w = m->work;
     cudaError_t e = m->prec == DG_FP64
                         ? dg::Launch<double>::rk_step(m->geo, m->ops64, (double *)Q, (double *)dQ,
@@ -323,12 +326,71 @@ dg_status dg_advance(const dg_mesh *m, void *Q, void *dQ, double cfl, int nsteps
     if (!m || !Q || !dQ || !dts || Q == dQ || !aligned16(Q) || !aligned16(dQ) || nsteps < 1 ||
         !(cfl > 0.0) || !std::isfinite(cfl))
         return DG_ERR_ARG;
+    if (m->geo.zlo) return DG_ERR_UNSUPPORTED;  // a slab's halos change between stages
     dg::Work w = m->work;
     cudaError_t e = m->prec == DG_FP64
                         ? dg::Launch<double>::advance(m->geo, m->ops64, (double *)Q, (double *)dQ,
                                                       cfl, nsteps, dts, integ, w, as_stream(stream))
                         : dg::Launch<float>::advance(m->geo, m->ops32, (float *)Q, (float *)dQ,
                                                      cfl, nsteps, dts, integ, w, as_stream(stream));
+    return cuda_status(e);
+}
+
+dg_status dg_rk_stage(const dg_mesh *m, const void *Qin, void *Qout, void *dQ,
+                      const double *dt_dev, int stage, void *stream)
+{
+    if (!m || !Qin || !Qout || !dQ || !dt_dev || stage < 0 || stage > 4) return DG_ERR_ARG;
+    if (Qin == dQ || Qout == dQ || !aligned16(Qin) || !aligned16(Qout) || !aligned16(dQ))
+        return DG_ERR_ARG;
+    if (m->prec == DG_FP32 && Qin == Qout) return DG_ERR_ARG;
+    dg::Work w = m->work;
+    cudaError_t e = m->prec == DG_FP64
+                        ? dg::Launch<double>::rk_stage(m->geo, m->ops64, (const double *)Qin,
+                                                       (double *)Qout, (double *)dQ, dt_dev, stage,
+                                                       w, as_stream(stream))
+                        : dg::Launch<float>::rk_stage(m->geo, m->ops32, (const float *)Qin,
+                                                      (float *)Qout, (float *)dQ, dt_dev, stage, w,
+                                                      as_stream(stream));
+    return cuda_status(e);
+}
+
+dg_status dg_mesh_set_zhalo(dg_mesh *m, const void *halo_lo, const void *halo_hi)
+{
+    if (!m || (!halo_lo) != (!halo_hi)) return DG_ERR_ARG;
+    if (!halo_lo) {
+        m->geo.zlo = m->geo.zhi = nullptr;
+        m->geo.zflux = nullptr;
+        return DG_OK;
+    }
+    if (m->prec == DG_FP32 && !dg::column_stage(m->geo.p + 1)) return DG_ERR_UNSUPPORTED;
+    if (m->prec == DG_FP64 && !m->work.zflux) {
+        const int N = m->geo.p + 1;
+        const size_t bytes = (size_t)dg::NF * (size_t)m->geo.nx * m->geo.ny * N * N * sizeof(double);
+        cudaError_t e = cudaMalloc(&m->work.zflux, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            m->work.zflux = nullptr;
+            return cuda_status(e);
+        }
+        m->ws_bytes += bytes;
+    }
+    m->geo.zlo = halo_lo;
+    m->geo.zhi = halo_hi;
+    m->geo.zflux = m->work.zflux;
+    return DG_OK;
+}
+
+dg_status dg_zhalo_traces(const dg_mesh *m, const void *Q, void *send_lo, void *send_hi,
+                          void *stream)
+{
+    if (!m || !Q || !send_lo || !send_hi || send_lo == send_hi) return DG_ERR_ARG;
+    cudaError_t e = m->prec == DG_FP64
+                        ? dg::Launch<double>::ztraces(m->geo, m->ops64, (const double *)Q,
+                                                      (double *)send_lo, (double *)send_hi,
+                                                      as_stream(stream))
+                        : dg::Launch<float>::ztraces(m->geo, m->ops32, (const float *)Q,
+                                                     (float *)send_lo, (float *)send_hi,
+                                                     as_stream(stream));
     return cuda_status(e);
 }
 

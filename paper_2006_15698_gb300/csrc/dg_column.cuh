@@ -380,11 +380,20 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
     column_prefetch<N, TX, TY, Ix>(Qin, slot_of(z0 + 1), g, ex0, ey0, txv, tyv, zmod(z0 + 1));
     cp_async_wait_all();
     __syncthreads();
+    // z slabs: the traces of another slab's layer, from the halo [NF][nx*ny][N^2]
+    auto halo_task = [&](const void *halo, int e2, int ln, int face) {
+        const Ix col = (Ix)(ex0 + e2 % TX) + (Ix)g.nx * (ey0 + e2 / TX);
+        const float *h = static_cast<const float *>(halo) + col * N2 + ln;
+        float *tt = sT + (size_t)e2 * TSTR + (face * NF) * N2 + ln;
+#pragma unroll
+        for (int n = 0; n < NF; ++n) tt[n * N2] = h[(Ix)n * plane * N2];
+    };
     for (int t = tid; t < 2 * EPB * N2; t += nthr) {
         const int w = t / (EPB * N2), r = t - w * (EPB * N2);
         const int e2 = r / N2, ln = r - e2 * N2;
         if (e2 % TX >= txv || e2 / TX >= tyv) continue;
-        if (w == 0) line_task<N, TX, TY, 2>(slot_of(z0 - 1), sT, lm, lp, e2, ln, 1);
+        if (w == 0 && g.zlo != nullptr && z0 == 0) halo_task(g.zlo, e2, ln, 5);
+        else if (w == 0) line_task<N, TX, TY, 2>(slot_of(z0 - 1), sT, lm, lp, e2, ln, 1);
         else line_task<N, TX, TY, 2>(slot_of(z0), sT, lm, lp, e2, ln, 0);
     }
     __syncthreads();
@@ -440,6 +449,7 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
             if (w == 0) line_task<N, TX, TY, 0>(cur, sT, lm, lp, e2, ln, 2);
             else if (w == 1) line_task<N, TX, TY, 1>(cur, sT, lm, lp, e2, ln, 2);
             else if (w == 2) line_task<N, TX, TY, 2>(cur, sT, lm, lp, e2, ln, 1);
+            else if (g.zhi != nullptr && z == g.nz - 1) halo_task(g.zhi, e2, ln, 4);
             else line_task<N, TX, TY, 2>(nxt, sT, lm, lp, e2, ln, 0);
         }
         __syncthreads();

@@ -45,6 +45,16 @@ struct Geo {
     double hmin;
     double xi[NMAX];   // Gauss-Legendre nodes on [-1, 1]
     double w[NMAX];    // Gauss-Legendre weights
+    // z slabs (dg_mesh_set_zhalo): when zlo is set, the mesh's z neighbours
+    // beyond its own layers are not the periodic wrap but another slab's
+    // layers, known only by their face traces, [NF][nx*ny][N^2] scalars of
+    // the state's type (face point j*N + i):
+    //   zlo   traces at the +z end of the layer below layer 0
+    //   zhi   traces at the -z end of the layer above layer nz-1
+    //   zflux (double form) the interface fluxes of the -z face of layer 0,
+    //         [NF][nx*ny][N^2], computed by the face kernel from zlo
+    const void *zlo, *zhi;
+    void *zflux;
 };
 
 // Per-kernel CUDA-event timing of a mesh handle (dg_profile_begin/end):
@@ -91,6 +101,7 @@ struct Work {
     unsigned long long *lam_bits = nullptr; // CFL maximum (bits of a positive double)
     int *err = nullptr;                     // sticky error flag
     void *qtmp = nullptr;                   // second state (float form's ping-pong)
+    void *zflux = nullptr;                  // -z interface fluxes of layer 0 (z slabs, double)
     Prof *prof = nullptr;                   // kernel timing (host object)
 };
 
@@ -192,6 +203,12 @@ struct Launch {
                            cudaStream_t s);
     static cudaError_t norms(const Geo &g, const real *Q, const real *Qref, double *out, Work &w,
                              cudaStream_t s);
+    // one LSERK45 stage (stage in 0..4) from Qin to Qout
+    static cudaError_t rk_stage(const Geo &g, const Ops<real> &ops, const real *Qin, real *Qout,
+                                real *dQ, const double *dt, int stage, Work &w, cudaStream_t s);
+    // z-face traces of the first and last layers (z slabs)
+    static cudaError_t ztraces(const Geo &g, const Ops<real> &ops, const real *Q, real *lo,
+                               real *hi, cudaStream_t s);
     // nsteps x (cfl time step -> dts[k], LSERK45 step, integrals -> integ[k * DG_NORMS_LEN])
     static cudaError_t advance(const Geo &g, const Ops<real> &ops, real *Q, real *dQ, double cfl,
                                int nsteps, double *dts, double *integ, Work &w, cudaStream_t s);

@@ -101,6 +101,28 @@ __device__ __forceinline__ double recip(double x)
 }
 __device__ __forceinline__ float recip(float x) { return 1.0f / x; }
 
+// sqrt(a) for the positive, finite, normal a = gamma p / rho of the sound
+// speed, on the FP64 pipe with fewer instructions than the correctly rounded
+// square root: the hardware reciprocal-square-root approximation y ~ a^-1/2
+// (rsqrt.approx.ftz.f64), one Newton-Raphson step y <- y + y (1 - a y^2)/2
+// (squares the relative error), then the root c = a y and one correction
+// c <- c + (y/2)(a - c^2) with the residual a - c^2 formed exactly by an FMA
+// (P. Markstein, "IA-64 and Elementary Functions", Prentice Hall 2000, the
+// coupled root / reciprocal-root iteration).  The result is within one ulp of
+// the correctly rounded root (checked against CUDA's sqrt on a sweep of
+// inputs, dg_selfcheck_sqrt).  a = 0 gives NaN (a zero pressure, which the
+// time-step reduction reports as non-physical).
+__device__ __forceinline__ double sqrt_pos(double a)
+{
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+    const double e = fma(-0.5 * a, y * y, 0.5);
+    y = fma(y, e, y);
+    const double c = a * y;
+    const double r = fma(-c, c, a);
+    return fma(r, 0.5 * y, c);
+}
+
 // Local Lax-Friedrichs (Rusanov) flux through a face with normal +e_DIR,
 // qL on the -side, qR on the +side (Sec. II.B; local dissipation speed):
 //   F* = (F(qL) + F(qR))/2 - max(|u_n| + c)/2 (qR - qL)
@@ -108,15 +130,34 @@ __device__ __forceinline__ float recip(float x) { return 1.0f / x; }
 // side's 1/rho, pressure and normal velocity are formed first and every flux
 // component F(q)_n = q_n u_n (+ p) is evaluated where it is combined, so
 // fewer values are live at once (the kernel's occupancy is register bound).
+// (Double: one reciprocal 1/(rhoL rhoR) serves both densities, and the
+// sound speeds use sqrt_pos; each result within a few ulp of the plain
+// formulas, well inside the FP64 form's tolerance.)
 template <int DIR, typename real>
 __device__ __forceinline__ void lf_flux2(const real qL[NF], const real qR[NF], real gamma,
                                          real gm1, real f[NF])
 {
-    const real rL = recip(qL[0]), rR = recip(qR[0]);
+    real rL, rR;
+    if constexpr (sizeof(real) == 8) {
+        const real rr = recip(qL[0] * qR[0]);
+        rL = qR[0] * rr;
+        rR = qL[0] * rr;
+    } else {
+        rL = recip(qL[0]);
+        rR = recip(qR[0]);
+    }
     const real pL = gm1 * (qL[4] - real(0.5) * (qL[1] * qL[1] + qL[2] * qL[2] + qL[3] * qL[3]) * rL);
     const real pR = gm1 * (qR[4] - real(0.5) * (qR[1] * qR[1] + qR[2] * qR[2] + qR[3] * qR[3]) * rR);
     const real uL = qL[1 + DIR] * rL, uR = qR[1 + DIR] * rR;
-    const real lam = fmax(fabs(uL) + sqrt(gamma * pL * rL), fabs(uR) + sqrt(gamma * pR * rR));
+    real cL, cR;
+    if constexpr (sizeof(real) == 8) {
+        cL = sqrt_pos(gamma * pL * rL);
+        cR = sqrt_pos(gamma * pR * rR);
+    } else {
+        cL = sqrt(gamma * pL * rL);
+        cR = sqrt(gamma * pR * rR);
+    }
+    const real lam = fmax(fabs(uL) + cL, fabs(uR) + cR);
     f[0] = (qL[1 + DIR] + qR[1 + DIR]) - lam * (qR[0] - qL[0]);
 #pragma unroll
     for (int n = 1; n < 4; ++n) {
@@ -131,10 +172,28 @@ __device__ __forceinline__ void lf_flux2(const real qL[NF], const real qR[NF], r
 // interface fluxes
 // ---------------------------------------------------------------------------
 
+// Trace sum_c l[c] a[c * stride] of a face-normal node line (double form),
+// every operation explicitly rounded in a fixed order, so that every kernel
+// computing the trace of the same line (the face kernel, the z-slab trace
+// kernel) gets the same value bit for bit.  (The float kernels' traces are
+// line_dot, dg_column.cuh.)
+template <int N>
+__device__ __forceinline__ double trace_line(const double *l, const double *__restrict__ a,
+                                             int stride)
+{
+    double s = __dmul_rn(l[0], __ldg(a));
+#pragma unroll
+    for (int c = 1; c < N; ++c) s = __fma_rn(l[c], __ldg(a + c * stride), s);
+    return s;
+}
+
 // One thread per (direction, element, face point) of the element's +DIR face.
 // Face point pt = t2*N + t1 where (t1, t2) are the two tangential node indices
 // in (i, j, k) order.  The element is the left state, its +DIR neighbour the
 // right state; each unique face of the periodic mesh is visited once.
+// z slabs (g.zlo set): the +z face of the last layer takes its right state
+// from the halo zhi, and layer 0's threads also evaluate their -z face
+// (left state from the halo zlo) into g.zflux, with the same code.
 template <int N, int DIR, typename real>
 __device__ __forceinline__ void face_point(const real *__restrict__ Q, real *__restrict__ F,
                                            const Ops<real> &T, const Geo &g, long long e, int pt)
@@ -143,25 +202,42 @@ __device__ __forceinline__ void face_point(const real *__restrict__ Q, real *__r
     const int t1 = pt % N, t2 = pt / N;
     const int base = DIR == 0 ? (t2 * N + t1) * N : (DIR == 1 ? t2 * N2 + t1 : t2 * N + t1);
     constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? N : N2);
-    const long long en = neighbour<DIR>(e, +1, g);
-    real qL[NF], qR[NF];
+    const long long plane = (long long)g.nx * g.ny;
+    const long long ez = DIR == 2 ? e / plane : 0;
+    const bool slab = DIR == 2 && g.zlo != nullptr;
+    const int faces = slab && ez == 0 ? 2 : 1;
+#pragma unroll 1
+    for (int side = 0; side < faces; ++side) {
+        // side 0: the +DIR face (this element left); side 1: the -z face of
+        // layer 0 of a slab (this element right, the halo left)
+        real qL[NF], qR[NF];
+        const long long en = neighbour<DIR>(e, +1, g);
+        const long long h = ((long long)0 * plane + (e - ez * plane)) * N2 + pt;  // halo index of field 0
 #pragma unroll
-    for (int n = 0; n < NF; ++n) {
-        const real *a = Q + sidx(n, e, base, g.E, N3);
-        const real *b = Q + sidx(n, en, base, g.E, N3);
-        real sl = real(0), sr = real(0);
-#pragma unroll
-        for (int c = 0; c < N; ++c) {
-            sl += T.lp[c] * __ldg(a + c * stride);
-            sr += T.lm[c] * __ldg(b + c * stride);
+        for (int n = 0; n < NF; ++n) {
+            const real *a = Q + sidx(n, e, base, g.E, N3);
+            if (side == 0) {
+                qL[n] = trace_line<N>(T.lp, a, stride);
+                if (slab && ez == g.nz - 1)
+                    qR[n] = static_cast<const real *>(g.zhi)[h + (long long)n * plane * N2];
+                else
+                    qR[n] = trace_line<N>(T.lm, Q + sidx(n, en, base, g.E, N3), stride);
+            } else {
+                qL[n] = static_cast<const real *>(g.zlo)[h + (long long)n * plane * N2];
+                qR[n] = trace_line<N>(T.lm, a, stride);
+            }
         }
-        qL[n] = sl;
-        qR[n] = sr;
-    }
-    real f[NF];
-    lf_flux2<DIR>(qL, qR, T.gamma, T.gm1, f);
+        real f[NF];
+        lf_flux2<DIR>(qL, qR, T.gamma, T.gm1, f);
+        if (side == 0) {
 #pragma unroll
-    for (int n = 0; n < NF; ++n) F[fidx(DIR, n, e, pt, g.E, N2)] = f[n];
+            for (int n = 0; n < NF; ++n) F[fidx(DIR, n, e, pt, g.E, N2)] = f[n];
+        } else {
+#pragma unroll
+            for (int n = 0; n < NF; ++n)
+                static_cast<real *>(g.zflux)[h + (long long)n * plane * N2] = f[n];
+        }
+    }
 }
 
 // CTA shape of face_flux_kernel: EF consecutive elements and all three of
@@ -264,6 +340,14 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
     const long long exm = neighbour<0>(e, -1, g);
     const long long eym = neighbour<1>(e, -1, g);
     const long long ezm = neighbour<2>(e, -1, g);
+    // z slabs: the -z face flux of layer 0 comes from the face kernel's zflux
+    const long long plane = (long long)g.nx * g.ny;
+    const real *fzm = F + fidx(2, 0, ezm, j * N + i, g.E, N2);
+    long long fzm_stride = g.E * N2;  // between fields
+    if (g.zflux != nullptr && e < plane) {
+        fzm = static_cast<const real *>(g.zflux) + e * N2 + j * N + i;
+        fzm_stride = plane * N2;
+    }
     const int px = k * N + j, py = k * N + i, pz = j * N + i;
     const real *Dx = sD + 0 * N2 + i * N, *Dy = sD + 1 * N2 + j * N, *Dz = sD + 2 * N2 + k * N;
 
@@ -286,7 +370,7 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
         acc -= sLp[1 * N + j] * __ldg(F + fidx(1, n, e, py, g.E, N2));
         acc += sLm[1 * N + j] * __ldg(F + fidx(1, n, eym, py, g.E, N2));
         acc -= sLp[2 * N + k] * __ldg(F + fidx(2, n, e, pz, g.E, N2));
-        acc += sLm[2 * N + k] * __ldg(F + fidx(2, n, ezm, pz, g.E, N2));
+        acc += sLm[2 * N + k] * __ldg(fzm + n * fzm_stride);
 
         const long long o = sidx(n, e, node, g.E, N3);
         if (MODE == 0) {
@@ -303,6 +387,41 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
 #include "dg_fused.cuh"
 #include "dg_column.cuh"
 #include "dg_lines.cuh"
+
+// z slabs: the face traces a slab sends to its neighbours, one thread per
+// (column element, face point): lo = layer 0's traces at its -z end,
+// hi = the last layer's traces at its +z end, in the halo layout
+// [NF][nx*ny][N^2], with the stage kernels' own trace arithmetic (double:
+// trace_line as face_point; float: line_dot as the column kernels).
+template <int N, typename real>
+__global__ void __launch_bounds__(256) ztraces_kernel(const real *__restrict__ Q, real *lo,
+                                                      real *hi, const Ops<real> T, const Geo g)
+{
+    constexpr int N2 = N * N, N3 = N * N * N;
+    const long long plane = (long long)g.nx * g.ny;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= plane * N2) return;
+    const long long col = t / N2;
+    const int pt = (int)(t - col * N2);
+    const long long top = col + (long long)(g.nz - 1) * plane;
+#pragma unroll
+    for (int n = 0; n < NF; ++n) {
+        const real *a = Q + sidx(n, col, pt, g.E, N3), *b = Q + sidx(n, top, pt, g.E, N3);
+        if constexpr (std::is_same<real, double>::value) {
+            lo[(n * plane + col) * N2 + pt] = trace_line<N>(T.lm, a, N2);
+            hi[(n * plane + col) * N2 + pt] = trace_line<N>(T.lp, b, N2);
+        } else {
+            float va[N], vb[N];
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                va[c] = __ldg(a + c * N2);
+                vb[c] = __ldg(b + c * N2);
+            }
+            lo[(n * plane + col) * N2 + pt] = line_dot<N>(T.lm, va);
+            hi[(n * plane + col) * N2 + pt] = line_dot<N>(T.lp, vb);
+        }
+    }
+}
 
 // ---------------------------------------------------------------------------
 // time step, integrals, initial states
@@ -987,6 +1106,8 @@ cudaError_t rhs_n(const Geo &g, const Ops<real> &T, const real *Q, real *R, Work
                   cudaStream_t s)
 {
     if constexpr (std::is_same<real, float>::value) {
+        // z slabs: only the column kernels read the halo traces
+        if (g.zlo != nullptr && !column_stage(N)) return cudaErrorNotSupported;
         if (column_stage(N))
             return launch_column<N, 0>(g, T, Q, R, nullptr, 0.0f, 0.0f, nullptr, w.prof, s);
         return launch_fused<N, 0>(g, T, Q, R, nullptr, 0.0f, 0.0f, nullptr, w.prof, s);
@@ -1037,6 +1158,40 @@ cudaError_t rk_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, const doub
         }
         return cudaSuccess;
     }
+}
+
+// One LSERK45 stage (st in 0..4) from Qin to Qout (dg_rk_stage): the double
+// form's two kernels (Qin == Qout allowed: the interface fluxes are complete
+// before the in-place update), or the float form's single-pass stage kernel
+// (Qout a different buffer: neighbouring CTAs still read Qin).
+template <int N, typename real>
+cudaError_t rk_stage_n(const Geo &g, const Ops<real> &T, const real *Qin, real *Qout, real *dQ,
+                       const double *dt, int st, Work &w, cudaStream_t s)
+{
+    if constexpr (std::is_same<real, float>::value) {
+        if (g.zlo != nullptr && !column_stage(N)) return cudaErrorNotSupported;
+        const float A = float(kRkA[st]), B = float(kRkB[st]);
+        return column_stage(N) ? launch_column<N, 1>(g, T, Qin, Qout, dQ, A, B, dt, w.prof, s)
+                               : launch_fused<N, 1>(g, T, Qin, Qout, dQ, A, B, dt, w.prof, s);
+    } else {
+        real *F = static_cast<real *>(w.face_flux);
+        cudaError_t err = launch_face<N>(g, T, Qin, F, w.prof, s);
+        if (err != cudaSuccess) return err;
+        return launch_volume<N, real, 1>(g, T, Qin, Qout, dQ, F, real(kRkA[st]), real(kRkB[st]),
+                                         dt, w.prof, s);
+    }
+}
+
+// z slabs: the face traces of the first and last layers (ztraces_kernel)
+template <int N, typename real>
+cudaError_t ztraces_n(const Geo &g, const Ops<real> &T, const real *Q, real *lo, real *hi,
+                      cudaStream_t s)
+{
+    const long long pts = (long long)g.nx * g.ny * N * N;
+    const long long blocks = (pts + 255) / 256;
+    if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
+    ztraces_kernel<N, real><<<(unsigned)blocks, 256, 0, s>>>(Q, lo, hi, T, g);
+    return cudaGetLastError();
 }
 
 // One float-form RK stage (MODE 1) of a single mesh from src to dst with the
@@ -1211,7 +1366,29 @@ cudaError_t advance_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, doubl
     KW cudaError_t advance_n<NN, REAL>(const Geo &, const Ops<REAL> &, REAL *, REAL *, double, \
                                        int, double *, double *, Work &, cudaStream_t);       \
     KW cudaError_t stage_n<NN, REAL>(const Geo &, const Ops<REAL> &, const REAL *, REAL *,     \
-                                     REAL *, REAL, REAL, const double *, cudaStream_t);
+                                     REAL *, REAL, REAL, const double *, cudaStream_t);      \
+    KW cudaError_t rk_stage_n<NN, REAL>(const Geo &, const Ops<REAL> &, const REAL *, REAL *,  \
+                                        REAL *, const double *, int, Work &, cudaStream_t);  \
+    KW cudaError_t ztraces_n<NN, REAL>(const Geo &, const Ops<REAL> &, const REAL *, REAL *,   \
+                                       REAL *, cudaStream_t);
+
+template <typename real>
+cudaError_t Launch<real>::rk_stage(const Geo &g, const Ops<real> &T, const real *Qin, real *Qout,
+                                   real *dQ, const double *dt, int stage, Work &w, cudaStream_t s)
+{
+#define DG_CALL(NN) rk_stage_n<NN, real>(g, T, Qin, Qout, dQ, dt, stage, w, s)
+    DG_DISPATCH_P(g.p, DG_CALL)
+#undef DG_CALL
+}
+
+template <typename real>
+cudaError_t Launch<real>::ztraces(const Geo &g, const Ops<real> &T, const real *Q, real *lo,
+                                  real *hi, cudaStream_t s)
+{
+#define DG_CALL(NN) ztraces_n<NN, real>(g, T, Q, lo, hi, s)
+    DG_DISPATCH_P(g.p, DG_CALL)
+#undef DG_CALL
+}
 
 template <typename real>
 cudaError_t Launch<real>::advance(const Geo &g, const Ops<real> &T, real *Q, real *dQ, double cfl,

@@ -300,13 +300,23 @@ __global__ void __launch_bounds__(
     const float *Lm = sOp + 3 * N2, *Lp = Lm + 3 * N;
     const float lmx = Lm[i], lmy = Lm[N + j], lpx = Lp[i], lpy = Lp[N + j];
 
-    // flux through the -z face of the line in the current layer
+    // z slabs: this line's face point in the halo layout [NF][nx*ny][N^2]
+    const Ix hcol = ((Ix)(ex0 + a) + (Ix)g.nx * (ey0 + b)) * N2 + j * N + i;
+    const Ix hstride = plane * N2;
+
+    // flux through the -z face of the line in the current layer (a slab's
+    // first layer: the layer below is another slab's, known by its traces)
     float fzm[NF];
     if (active) {
         float v[NF][N], tp[NF], tm[NF];
-        load_zline(slot_of(z0 - 1), v);
+        if (g.zlo != nullptr && z0 == 0) {
 #pragma unroll
-        for (int n = 0; n < NF; ++n) tp[n] = line_dot<N>(lpr, v[n]);
+            for (int n = 0; n < NF; ++n) tp[n] = static_cast<const float *>(g.zlo)[hcol + n * hstride];
+        } else {
+            load_zline(slot_of(z0 - 1), v);
+#pragma unroll
+            for (int n = 0; n < NF; ++n) tp[n] = line_dot<N>(lpr, v[n]);
+        }
         load_zline(slot_of(z0), v);
 #pragma unroll
         for (int n = 0; n < NF; ++n) tm[n] = line_dot<N>(lmr, v[n]);
@@ -378,11 +388,20 @@ __global__ void __launch_bounds__(
                 }
             }
             float v[NF][N], tp[NF], tm[NF];
-            load_zline(nxt, v);
+            if (g.zhi != nullptr && z == g.nz - 1) {
+                // a slab's last layer: the layer above is another slab's
 #pragma unroll
-            for (int n = 0; n < NF; ++n) {
-                tp[n] = line_dot<N>(lpr, qc[n]);
-                tm[n] = line_dot<N>(lmr, v[n]);
+                for (int n = 0; n < NF; ++n) {
+                    tp[n] = line_dot<N>(lpr, qc[n]);
+                    tm[n] = static_cast<const float *>(g.zhi)[hcol + n * hstride];
+                }
+            } else {
+                load_zline(nxt, v);
+#pragma unroll
+                for (int n = 0; n < NF; ++n) {
+                    tp[n] = line_dot<N>(lpr, qc[n]);
+                    tm[n] = line_dot<N>(lmr, v[n]);
+                }
             }
             lf_flux2_f<2>(tp, tm, gamma, gm1, fzp);
         }

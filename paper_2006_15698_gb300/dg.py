@@ -55,6 +55,12 @@ _lib.dg_norms.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.dg_norms.restype = ctypes.c_int
 _lib.dg_advance.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _vp, _vp, _vp]
 _lib.dg_advance.restype = ctypes.c_int
+_lib.dg_rk_stage.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
+_lib.dg_rk_stage.restype = ctypes.c_int
+_lib.dg_mesh_set_zhalo.argtypes = [_vp, _vp, _vp]
+_lib.dg_mesh_set_zhalo.restype = ctypes.c_int
+_lib.dg_zhalo_traces.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.dg_zhalo_traces.restype = ctypes.c_int
 _lib.dg_status_string.argtypes = [ctypes.c_int]
 _lib.dg_status_string.restype = ctypes.c_char_p
 _lib.dg_last_error.argtypes = [_vp]
@@ -125,6 +131,34 @@ def dg_fma_throughput(precision):
     _check(_lib.dg_fma_throughput(precision, ctypes.byref(f), ctypes.byref(ms)),
            "dg_fma_throughput")
     return f.value, ms.value
+
+
+_lib.dg_dmma_throughput.argtypes = [ctypes.c_int, _dp, _dp]
+_lib.dg_dmma_throughput.restype = ctypes.c_int
+
+
+def dg_dmma_throughput(mix=False):
+    """(flop/s, ms) of FP64 mma.sync m8n8k4 chains on the current device
+    (mix: odd warps run FP64 FMA chains of the same flop count instead)."""
+    f, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.dg_dmma_throughput(1 if mix else 0, ctypes.byref(f), ctypes.byref(ms)),
+           "dg_dmma_throughput")
+    return f.value, ms.value
+
+
+_lib.dg_selfcheck_sqrt.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp]
+_lib.dg_selfcheck_sqrt.restype = ctypes.c_int
+
+
+def dg_selfcheck_sqrt(a, stream=None):
+    """(fast, ieee): the double kernels' sound-speed root and CUDA's sqrt of
+    the positive float64 CUDA tensor a."""
+    if a.dtype != torch.float64 or not a.is_cuda or not a.is_contiguous():
+        raise ValueError("a must be a contiguous float64 CUDA tensor")
+    fast, ieee = torch.empty_like(a), torch.empty_like(a)
+    _check(_lib.dg_selfcheck_sqrt(_ptr(a), _ptr(fast), _ptr(ieee), a.numel(), _stream(stream)),
+           "dg_selfcheck_sqrt")
+    return fast, ieee
 
 
 DG_PROFILE_KINDS = 8
@@ -200,6 +234,20 @@ def dg_norms(h, Q, Qref, out_dev, stream=None):
 def dg_advance(h, Q, dQ, cfl, nsteps, dts_dev, integ_dev, stream=None):
     _check(_lib.dg_advance(h, _ptr(Q), _ptr(dQ), cfl, nsteps, _ptr(dts_dev), _ptr(integ_dev),
                            _stream(stream)), "dg_advance")
+
+
+def dg_rk_stage(h, Qin, Qout, dQ, dt_dev, stage, stream=None):
+    _check(_lib.dg_rk_stage(h, _ptr(Qin), _ptr(Qout), _ptr(dQ), _ptr(dt_dev), int(stage),
+                            _stream(stream)), "dg_rk_stage")
+
+
+def dg_mesh_set_zhalo(h, halo_lo, halo_hi):
+    _check(_lib.dg_mesh_set_zhalo(h, _ptr(halo_lo), _ptr(halo_hi)), "dg_mesh_set_zhalo")
+
+
+def dg_zhalo_traces(h, Q, send_lo, send_hi, stream=None):
+    _check(_lib.dg_zhalo_traces(h, _ptr(Q), _ptr(send_lo), _ptr(send_hi), _stream(stream)),
+           "dg_zhalo_traces")
 
 
 def dg_status_string(st):
@@ -322,6 +370,43 @@ class Mesh:
             integ = torch.empty((nsteps, DG_NORMS_LEN), dtype=torch.float64, device=self.device)
         dg_advance(self.h, self._chk(Q), self._chk(dQ), cfl, nsteps, dts, integ, stream)
         return dts, integ
+
+    def rk_stage(self, Qin, Qout, dQ, dt, stage, stream=None):
+        """LSERK45 stage `stage` (0..4): dQ <- A dQ + dt R(Qin), Qout <- Qin + B dQ."""
+        dg_rk_stage(self.h, self._chk(Qin), self._chk(Qout), self._chk(dQ), dt, stage, stream)
+
+    # --- z slabs -----------------------------------------------------------
+    @property
+    def halo_shape(self):
+        """Shape of a halo / trace buffer: (5, nx*ny, N*N)."""
+        return (NF, self.nx * self.ny, self.N * self.N)
+
+    def empty_halo(self):
+        return torch.empty(self.halo_shape, dtype=self.dtype, device=self.device)
+
+    def _chk_halo(self, t):
+        if (t.dtype != self.dtype or not t.is_cuda or not t.is_contiguous()
+                or t.numel() != NF * self.nx * self.ny * self.N * self.N):
+            raise ValueError(f"halo tensor must be a contiguous CUDA tensor of {self.halo_shape} "
+                             f"and dtype {self.dtype}")
+        return t
+
+    def set_zhalo(self, halo_lo, halo_hi):
+        """Make the z boundary an interface to other slabs whose traces the
+        two halo tensors hold (kept by reference; None, None: periodic)."""
+        if halo_lo is None and halo_hi is None:
+            dg_mesh_set_zhalo(self.h, None, None)
+            self._halos = None
+            return
+        dg_mesh_set_zhalo(self.h, self._chk_halo(halo_lo), self._chk_halo(halo_hi))
+        self._halos = (halo_lo, halo_hi)  # the library keeps the pointers
+
+    def ztraces(self, Q, send_lo=None, send_hi=None, stream=None):
+        """(send_lo, send_hi): layer 0's -z-end and the last layer's +z-end traces."""
+        send_lo = self.empty_halo() if send_lo is None else self._chk_halo(send_lo)
+        send_hi = self.empty_halo() if send_hi is None else self._chk_halo(send_hi)
+        dg_zhalo_traces(self.h, self._chk(Q), send_lo, send_hi, stream)
+        return send_lo, send_hi
 
     def last_error(self):
         return dg_last_error(self.h)

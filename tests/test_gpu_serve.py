@@ -38,6 +38,7 @@ def test_mixed_cfl_alone_equals_in_the_mix():
                                L=10.0)
     for i, q in enumerate(reqs):
         q.cfl = (0.3, 0.5, 0.8)[i % 3]
+        q.arrival = 0.0  # all present at once: every CFL group active together
     budget = 8 * max(q.device_bytes() for q in reqs)
     mix = serve.Server(serve.GpuExecutor(), budget, keep_states=True).run(reqs)
     assert len(mix.outcomes) == len(reqs) and mix.peak_active >= 3
