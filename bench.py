@@ -136,7 +136,9 @@ def run_serve(args, w):
             "serving": {"p50_time_to_solution_s": s["p50_s"], "p99_time_to_solution_s": s["p99_s"],
                         "requests_per_s": s["requests_per_s"], "wall_s": s["wall_s"],
                         "peak_active": s["peak_active"], "peak_bytes": s["peak_bytes"],
-                        "batch_rebuilds": s["batch_rebuilds"], "iterations": s["iterations"]},
+                        "batch_rebuilds": s["batch_rebuilds"], "iterations": s["iterations"],
+                        "host_rebuild_s": s["rebuild_s"], "host_enqueue_s": s["enqueue_s"],
+                        "host_wait_s": s["wait_s"]},
             "clocks": ck}
 
 

@@ -278,7 +278,8 @@ int dg_get_tile_variant(int p);
 
 /* Stage kernel of the DG_FP32 single-mesh path (an implementation choice,
  * not in the paper), per degree in a process-wide table like the tile table
- * above (same threading rule; batches always use tiles):
+ * above (same threading rule; a batch's shared instances always run the line
+ * kernel, its own-launch instances follow this table):
  *   DG_STAGE_TILE    one CTA per tile of one z layer (the tile variant above);
  *                    the neighbour's face-normal lines read through L2
  *   DG_STAGE_COLUMN  one CTA per column of elements, walking up a chunk of z
@@ -300,38 +301,38 @@ int dg_get_stage_kernel(int p);
  * Each instance is a periodic box like a dg_mesh (same meaning of nx..gamma)
  * with caller-owned float device states Q (the solution) and dQ (the RK
  * register), in the layout above.  dg_batch_create computes every instance's
- * operators, allocates one second state per instance (the fused stage's
- * ping-pong buffer), the per-instance time steps and a work list of every
- * tile of every instance (the tile per degree that best fills a 256-thread
- * block, the tuning table deciding among equally full ones), grouped by
- * degree.  dg_batch_step advances every instance by nsteps LSERK45 steps,
- * each with its own CFL time step (same rule as dg_cfl_dt): per step one
- * persistent launch computes all time steps, then one persistent launch per
- * RK stage runs every tile of every instance (device dispatch on the degree;
- * a second launch per stage only for p = 6 instances, whose tiles need 352
- * threads).  Instances of at least dg_get_batch_direct_nodes() nodes
- * (default 2^13) are not in the work list: each
- * runs the single-mesh stage kernel of its degree (dg_set_stage_kernel) in
- * launches of its own, on up to four streams the batch owns, forked from
+ * operators, allocates one second state per instance (the stage's ping-pong
+ * buffer) unless the caller gives one, and the per-instance time steps.
+ * dg_batch_step advances every instance by nsteps LSERK45 steps, each with
+ * its own CFL time step (same rule as dg_cfl_dt): per step one launch
+ * computes all the shared instances' time steps, then, per RK stage, one
+ * launch per polynomial degree runs the single-mesh line stage kernel's body
+ * (DG_STAGE_LINES) over work items (instance, column of elements, chunk of
+ * at most 8 z layers) of every shared instance of that degree.  Instances of
+ * at least dg_get_batch_direct_nodes() nodes (default 2^13) are not shared:
+ * each runs the single-mesh stage kernel of its degree (dg_set_stage_kernel)
+ * in launches of its own, on up to four streams the batch owns, forked from
  * `stream` after the time steps and joined back to it at the end of every
- * step, so that they overlap one another and the persistent launches; the
- * results are those of the same mesh stepped alone, bit for bit.  The
- * stages alternate between Q and the batch's second states,
+ * step, so that they overlap one another and the shared launches.  Either
+ * way an instance's result is that of the same mesh stepped alone with the
+ * same stage kernel (the line kernel for shared instances), bit for bit.
+ * The stages alternate between Q and the batch's second states,
  * so an even number of steps ends in Q by itself; after an odd number the
  * second states are copied back (one device memcpy per instance).  With
  * use_graph != 0 the launches of two steps (and of one step) are recorded
  * once into CUDA graphs on `stream` (a created stream, not the legacy
  * default) and replayed; a changed cfl records new graphs.  Calls on one
  * batch must be ordered.
- * dg_batch_dt copies the time steps of the last step to a HOST array of n
- * doubles (synchronises); dg_batch_norms writes instance idx's integrals as
- * dg_norms does; dg_batch_state_init fills instance idx's Q like
+ * dg_batch_sizes returns the total DOF and the number of shared stage work
+ * items; dg_batch_dt copies the time steps of the last step to a HOST array
+ * of n doubles (synchronises); dg_batch_norms writes instance idx's
+ * integrals as dg_norms does; dg_batch_state_init fills instance idx's Q like
  * dg_state_init; dg_batch_last_error reads and clears the batch's
  * non-finite flag.  Errors as for dg_mesh_create and dg_rk_step.
  * dg_set_batch_direct_nodes sets that size threshold for batches created
  * afterwards (process-wide, like the tuning tables; 0: every instance runs its
- * own launches; INT64_MAX: all share the persistent launches); DG_ERR_ARG for
- * a negative value. */
+ * own launches; INT64_MAX: all are shared); DG_ERR_ARG for a negative
+ * value. */
 typedef struct {
     int nx, ny, nz, p;
     double x0, y0, z0, Lx, Ly, Lz, gamma;

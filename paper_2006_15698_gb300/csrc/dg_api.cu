@@ -564,16 +564,19 @@ dg_status dg_tile_shape(int p, int variant, int *tx, int *ty)
 struct dg_batch {
     int n = 0;
     std::vector<dg::InstDev> inst;      // host copy of the descriptors
-    std::vector<dg::BatchItem> items;   // host copy of the work list
+    std::vector<dg::LambdaItem> items;  // node ranges of the shared instances (time steps)
+    std::vector<dg::LineItem> litems;   // their stage work items, grouped by order N
     std::vector<long long> dofs;
     dg::InstDev *d_inst = nullptr;
-    dg::BatchItem *d_items = nullptr;
+    dg::LambdaItem *d_items = nullptr;
+    dg::LineItem *d_litems = nullptr;
+    int lbeg[dg::NMAX + 1] = {}, lend[dg::NMAX + 1] = {};  // work items of order N
     double *d_dt = nullptr;
     unsigned long long *d_lam = nullptr;
     int *d_err = nullptr;
     double *d_partials = nullptr;
     std::vector<void *> qt;             // second states owned by the batch
-    int threads = 256, grid = 1;    // CFL launches
+    int grid = 1;                   // CTAs of the time-step launch
     bool small = true;              // every instance's offsets fit a 32-bit int
     std::vector<int> direct;        // large instances: launched by themselves
     // streams the large instances' stage launches run on, concurrently with
@@ -581,13 +584,11 @@ struct dg_batch {
     // the caller's stream every step); lane_of[k]: the lane of direct[k]
     static constexpr int kLanes = 4;
     int nlanes = 0;
+    int group_lane[dg::NMAX + 1] = {};  // lane of the shared instances of order N
     cudaStream_t lane[kLanes] = {};
     cudaEvent_t fork_ev = nullptr;
     cudaEvent_t join_ev[kLanes] = {};
     std::vector<int> lane_of;
-    // per size class of the stage kernel: item range, shared memory, grid
-    int cbeg[2] = {0, 0}, cend[2] = {0, 0}, cgrid[2] = {1, 1};
-    size_t csmem[2] = {0, 0};
     // recorded graphs of one step (ends with the copy back) and of two steps
     // (ends in Q by itself), and the cfl they were recorded with
     cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
@@ -610,6 +611,7 @@ void batch_free(dg_batch *b)
     for (void *p : b->qt) cudaFree(p);
     cudaFree(b->d_inst);
     cudaFree(b->d_items);
+    cudaFree(b->d_litems);
     cudaFree(b->d_dt);
     cudaFree(b->d_lam);
     cudaFree(b->d_err);
@@ -622,29 +624,6 @@ void batch_free(dg_batch *b)
 // batch's lanes); the smaller ones share the persistent batched launches.
 // Process-wide, read by dg_batch_create (dg_set_batch_direct_nodes).
 std::atomic<long long> g_direct_nodes{1LL << 13};
-
-// Tile variant of order N inside a batch.  The batch runs every tile with one
-// block size (256 threads, 352 when a p = 6 instance is present), so the tile
-// that fills a block best is taken: the variants with the most nodes not
-// above 256 (all of them above 256 only for N = 7); among those, the tuning
-// table's choice if it is one of them, else the first.
-int batch_tile_variant(int N)
-{
-    int best_nodes = -1, pick = 0;
-    const int tuned = dg::tile_variant(N);
-    for (int v = 0; v < 8; ++v) {
-        int tx, ty, th;
-        size_t sm;
-        if (!dg::tile_code_info(N * 8 + v, &tx, &ty, &th, &sm)) break;
-        const int nodes = tx * ty * N * N * N;
-        const int score = nodes <= 256 ? nodes : 0;
-        if (score > best_nodes || (score == best_nodes && v == tuned)) {
-            best_nodes = score;
-            pick = v;
-        }
-    }
-    return pick;
-}
 
 // The kernels of `nsteps` (1 or 2) steps on stream s.  Per step: the CFL
 // time step of every instance (read from the buffer holding the state), then
@@ -667,7 +646,7 @@ cudaError_t batch_enqueue(const dg_batch *b, double cfl, int nsteps, cudaStream_
     cudaError_t e = cudaSuccess;
     int parity = 0;  // 0: the state is in Q at the start of the step
     for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
-        e = dg::batch_lambda(b->d_items, ni, b->d_inst, parity, b->d_err, b->grid, b->threads, s);
+        e = dg::batch_lambda(b->d_items, ni, b->d_inst, parity, b->d_err, b->grid, s);
         for (size_t k = 0; k < b->direct.size() && e == cudaSuccess; ++k) {
             const dg::InstDev &I = b->inst[b->direct[k]];
             e = dg::float_lambda(I.g, parity == 0 ? I.Q : I.Qt, I.lam_bits, b->d_err, s);
@@ -684,16 +663,21 @@ cudaError_t batch_enqueue(const dg_batch *b, double cfl, int nsteps, cudaStream_
             for (int st = 0; st < 5 && e == cudaSuccess; ++st) {
                 const int par = parity ^ (st & 1);
                 e = dg::float_stage(I.g, I.T, par == 0 ? I.Q : I.Qt, par == 0 ? I.Qt : I.Q, I.dQ,
-                                    (float)kA[st], (float)kB[st], I.dt, b->lane[b->lane_of[k]]);
+                                    (float)kA[st], (float)kB[st], I.dt,
+                                    b->nlanes > 0 ? b->lane[b->lane_of[k]] : s);
             }
         }
-        // the small instances' persistent launches on the caller's stream
-        for (int st = 0; st < 5 && e == cudaSuccess; ++st)
-            for (int c = 0; c < 2 && e == cudaSuccess; ++c)
-                if (b->cend[c] > b->cbeg[c])
-                    e = dg::batch_stage(b->d_items + b->cbeg[c], b->cend[c] - b->cbeg[c],
-                                        b->d_inst, parity ^ (st & 1), (float)kA[st], (float)kB[st],
-                                        c, b->small, b->cgrid[c], b->csmem[c], s);
+        // the shared instances: per order N one launch per stage (one CTA per
+        // instance, column and z chunk), on the order's lane (or the caller's
+        // stream when the batch has a single unit of work)
+        for (int N = 1; N <= dg::NMAX && e == cudaSuccess; ++N) {
+            if (b->lend[N] <= b->lbeg[N]) continue;
+            cudaStream_t ls = b->nlanes > 0 ? b->lane[b->group_lane[N]] : s;
+            for (int st = 0; st < 5 && e == cudaSuccess; ++st)
+                e = dg::batch_line_stage(b->d_litems + b->lbeg[N], b->lend[N] - b->lbeg[N],
+                                         b->d_inst, N, parity ^ (st & 1), (float)kA[st],
+                                         (float)kB[st], b->small, ls);
+        }
         for (int l = 0; l < b->nlanes && e == cudaSuccess; ++l) {
             e = cudaEventRecord(b->join_ev[l], b->lane[l]);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join_ev[l], 0);
@@ -761,7 +745,6 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
         fill_gas(d.gamma, I.T);
         I.Q = (float *)d.Q;
         I.dQ = (float *)d.dQ;
-        I.code = N * 8 + batch_tile_variant(N);
         const size_t bytes = (size_t)dg::NF * (size_t)g.E * N * N * N * sizeof(float);
         void *qt = d.Qt;
         if (!qt) {
@@ -785,35 +768,87 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
         batch_free(b);
         return st;
     }
-    // work list: every tile of every instance, grouped by tile code
+    // time-step work list: every shared instance's nodes in ranges of at
+    // most kLambdaNodes
     for (int i = 0; i < n; ++i) {
         dg::InstDev &I = b->inst[i];
         I.dt = b->d_dt + i;
         I.lam_bits = b->d_lam + i;
-        int tx, ty, th;
-        size_t sm;
-        if (!dg::tile_code_info(I.code, &tx, &ty, &th, &sm)) {
-            batch_free(b);
-            return DG_ERR_UNSUPPORTED;
-        }
         if (b->dofs[i] >= direct_nodes) {  // own launches
             b->direct.push_back(i);
             continue;
         }
-        const int c = dg::batch_code_class(I.code);
-        b->csmem[c] = std::max(b->csmem[c], sm);
-        const long long nt = dg::tile_count(I.g, tx, ty);
-        for (long long t = 0; t < nt; ++t) b->items.push_back({i, I.code, t});
+        for (long long t = 0; t < b->dofs[i]; t += dg::kLambdaNodes)
+            b->items.push_back({i, t, std::min(b->dofs[i], t + dg::kLambdaNodes)});
+        int lx, ly;
+        if (!dg::line_shape_info(I.g.p + 1, &lx, &ly)) {
+            batch_free(b);
+            return DG_ERR_UNSUPPORTED;
+        }
     }
-    std::stable_sort(b->items.begin(), b->items.end(),
-                     [](const dg::BatchItem &x, const dg::BatchItem &y) { return x.code < y.code; });
+    // stage work items: the line kernel's columns of the shared instances,
+    // each cut into z chunks.  Per order N one chunk length for all its
+    // instances, chosen as a single mesh's launch chooses it: the length that
+    // minimises (waves of the GPU's resident CTAs) x (layers per chunk + the
+    // chunk's extra prologue layer) over the order's columns.
+    {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        for (int N = 1; N <= dg::NMAX; ++N) {
+            std::vector<int> members;
+            int maxz = 0;
+            for (int i = 0; i < n; ++i)
+                if (b->inst[i].g.p + 1 == N && b->dofs[i] < direct_nodes) {
+                    members.push_back(i);
+                    maxz = std::max(maxz, b->inst[i].g.nz);
+                }
+            if (members.empty()) continue;
+            int lx, ly;
+            dg::line_shape_info(N, &lx, &ly);
+            const int per_sm = dg::batch_line_blocks_per_sm(N, b->small);
+            const long long resident = (long long)std::max(1, sms) * std::max(1, per_sm);
+            auto ncols = [&](int i) {
+                const dg::Geo &g = b->inst[i].g;
+                return (long long)((g.nx + lx - 1) / lx) * ((g.ny + ly - 1) / ly);
+            };
+            int best_zc = maxz;
+            double best = -1.0;
+            for (int zc = 1; zc <= maxz; ++zc) {
+                long long ctas = 0;
+                for (int i : members) ctas += ncols(i) * ((b->inst[i].g.nz + zc - 1) / zc);
+                const double cost = (double)((ctas + resident - 1) / resident) * (zc + 1);
+                if (best < 0.0 || cost < best) { best = cost; best_zc = zc; }
+            }
+            b->lbeg[N] = (int)b->litems.size();
+            for (int i : members) {
+                const int zc = std::min(best_zc, b->inst[i].g.nz);
+                const long long nblk = ncols(i) * ((b->inst[i].g.nz + zc - 1) / zc);
+                if (nblk > 0x7fffffffLL) {
+                    batch_free(b);
+                    return DG_ERR_ARG;
+                }
+                for (long long k = 0; k < nblk; ++k) b->litems.push_back({i, (int)k, zc});
+            }
+            b->lend[N] = (int)b->litems.size();
+        }
+    }
+    if (b->litems.size() > 0x7fffffffULL || b->items.size() > 0x7fffffffULL) {
+        batch_free(b);
+        return DG_ERR_ARG;
+    }
     err = cudaMalloc((void **)&b->d_inst, sizeof(dg::InstDev) * n);
     if (err == cudaSuccess && !b->items.empty())
-        err = cudaMalloc((void **)&b->d_items, sizeof(dg::BatchItem) * b->items.size());
+        err = cudaMalloc((void **)&b->d_items, sizeof(dg::LambdaItem) * b->items.size());
+    if (err == cudaSuccess && !b->litems.empty())
+        err = cudaMalloc((void **)&b->d_litems, sizeof(dg::LineItem) * b->litems.size());
     if (err == cudaSuccess)
         err = cudaMemcpy(b->d_inst, b->inst.data(), sizeof(dg::InstDev) * n, cudaMemcpyHostToDevice);
     if (err == cudaSuccess && !b->items.empty())
-        err = cudaMemcpy(b->d_items, b->items.data(), sizeof(dg::BatchItem) * b->items.size(),
+        err = cudaMemcpy(b->d_items, b->items.data(), sizeof(dg::LambdaItem) * b->items.size(),
+                         cudaMemcpyHostToDevice);
+    if (err == cudaSuccess && !b->litems.empty())
+        err = cudaMemcpy(b->d_litems, b->litems.data(), sizeof(dg::LineItem) * b->litems.size(),
                          cudaMemcpyHostToDevice);
     if (err != cudaSuccess) {
         dg_status st = cuda_status(err);
@@ -821,37 +856,43 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
         batch_free(b);
         return st;
     }
-    // persistent grids: as many CTAs as fit on the GPU at once, per size
-    // class (the items are sorted by code, so each class is one range)
+    // grid of the time-step reduction over the tiles: as many CTAs as fit
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int ni = (int)b->items.size();
-    int split = 0;
-    while (split < ni && dg::batch_code_class(b->items[split].code) == 0) ++split;
-    b->cbeg[0] = 0; b->cend[0] = split;
-    b->cbeg[1] = split; b->cend[1] = ni;
-    for (int c = 0; c < 2; ++c) {
-        const long long cnt = b->cend[c] - b->cbeg[c];
-        if (cnt == 0) continue;
-        const long long per_sm = dg::batch_stage_blocks_per_sm(c, b->small, b->csmem[c]);
-        b->cgrid[c] = (int)std::min<long long>((long long)sms * per_sm, cnt);
-    }
     b->grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * 8, (long long)ni));
-    // lanes for the large instances: largest first onto the least loaded lane
-    if (!b->direct.empty()) {
-        b->nlanes = (int)std::min<size_t>(dg_batch::kLanes, b->direct.size());
-        std::vector<int> order(b->direct.size());
+    // lanes: the units of stage work -- each large instance, and the shared
+    // instances of each order N (one launch per stage) -- largest first onto
+    // the least loaded lane
+    std::vector<long long> unit_dof;  // direct instances first, then the orders
+    std::vector<int> unit_N;
+    for (int k : b->direct) {
+        unit_dof.push_back(b->dofs[k]);
+        unit_N.push_back(0);
+    }
+    for (int N = 1; N <= dg::NMAX; ++N) {
+        if (b->lend[N] <= b->lbeg[N]) continue;
+        long long d = 0;
+        for (int i = 0; i < n; ++i)
+            if (b->inst[i].g.p + 1 == N && std::find(b->direct.begin(), b->direct.end(), i) == b->direct.end())
+                d += b->dofs[i];
+        unit_dof.push_back(d);
+        unit_N.push_back(N);
+    }
+    b->lane_of.assign(b->direct.size(), 0);
+    if (unit_dof.size() > 1) {
+        b->nlanes = (int)std::min<size_t>(dg_batch::kLanes, unit_dof.size());
+        std::vector<int> order(unit_dof.size());
         for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-            return b->dofs[b->direct[x]] > b->dofs[b->direct[y]];
-        });
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return unit_dof[x] > unit_dof[y]; });
         std::vector<long long> load(b->nlanes, 0);
-        b->lane_of.assign(b->direct.size(), 0);
         for (int k : order) {
             const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-            b->lane_of[k] = l;
-            load[l] += b->dofs[b->direct[k]];
+            if (unit_N[k] == 0) b->lane_of[k] = l;
+            else b->group_lane[unit_N[k]] = l;
+            load[l] += unit_dof[k];
         }
         err = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
         for (int l = 0; l < b->nlanes && err == cudaSuccess; ++l) {
@@ -886,7 +927,7 @@ dg_status dg_batch_sizes(const dg_batch *b, int64_t *n_dof, int64_t *n_items)
     long long s = 0;
     for (long long d : b->dofs) s += d;
     if (n_dof) *n_dof = s;
-    if (n_items) *n_items = (int64_t)b->items.size();
+    if (n_items) *n_items = (int64_t)b->litems.size();
     return DG_OK;
 }
 

@@ -383,120 +383,46 @@ __global__ void __launch_bounds__(FusedTile<N, TileShape<N, V>::TX, TileShape<N,
 }
 
 // ---------------------------------------------------------------------------
-// batches: many independent meshes, one persistent launch per stage
+// batches: the time-step reduction over many independent meshes (their
+// stages run batched_line_kernel, dg_lines.cuh)
 // ---------------------------------------------------------------------------
 
 #define DG_FOR_EACH_CODE(X) \
     X(1, 0) X(1, 1) X(2, 0) X(2, 1) X(2, 2) X(3, 0) X(3, 1) X(4, 0) X(4, 1) X(5, 0) X(5, 1) \
     X(6, 0) X(7, 0)
 
-// Two size classes, so that the registers of the large p = 6 tiles do not
-// cap the occupancy of all the others: class 0 holds the tile codes with
-// N <= 6 (every tile fits 256 threads; four resident CTAs bound registers to
-// 64), class 1 the N = 7 tiles (343 nodes, 352 threads).
-// One tile of a batch, compiled as a separate function: each tile code keeps
-// its own register allocation instead of sharing the switch's worst case.
-template <int N, int V, int MODE, typename Ix>
-__device__ __noinline__ void batched_tile(const float *__restrict__ Qin, float *__restrict__ Out,
-                                          float *__restrict__ dQ, const Ops<float> &T,
-                                          const Geo &g, long long tile, float A, float B,
-                                          float dtr, unsigned char *smem)
+// Lambda of the shared instances of a batch: work item k covers the nodes
+// [begin, end) of one instance (equal ranges of at most kLambdaNodes); a CTA
+// takes items in turn, evaluates the node speeds in float (node_speed_f, as
+// cfl_kernel for a float state), keeps their maximum in float and merges it
+// into the instance's Lambda slot as a double (bit patterns of non-negative
+// doubles; NaN, above every finite value, for a bad node).
+static __global__ void __launch_bounds__(256)
+    batched_lambda_kernel(const LambdaItem *__restrict__ items, int nitems,
+                          const InstDev *__restrict__ inst, int parity, int *err)
 {
-    fused_tile<N, TileShape<N, V>::TX, TileShape<N, V>::TY, MODE, Ix>(Qin, Out, dQ, T, g, tile, A,
-                                                                       B, dtr, smem);
-}
-
-#define DG_FOR_EACH_CODE_C0(X) \
-    X(1, 0) X(1, 1) X(2, 0) X(2, 1) X(2, 2) X(3, 0) X(3, 1) X(4, 0) X(4, 1) X(5, 0) X(5, 1) \
-    X(6, 0)
-#define DG_FOR_EACH_CODE_C1(X) X(7, 0)
-constexpr int kBatchClassThreads[2] = {256, 352};
-__host__ __device__ constexpr int batch_class(int code) { return (code >> 3) == 7 ? 1 : 0; }
-
-// Ix: index type of every instance's arrays (int when all offsets fit).
-template <int MODE, int CLASS, typename Ix>
-__global__ void __launch_bounds__(CLASS == 0 ? 256 : 352, CLASS == 0 ? 4 : 2)
-    batched_stage_kernel(const BatchItem *__restrict__ items, int nitems,
-                         const InstDev *__restrict__ inst, int parity, float A, float B)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const BatchItem item = items[it];
+        const LambdaItem item = items[it];
         const InstDev &d = inst[item.inst];
-        const float *src = parity == 0 ? d.Q : d.Qt;
-        float *dst = parity == 0 ? d.Qt : d.Q;
-        const float dtr = MODE != 0 ? (float)(*d.dt) : 0.0f;
-#define DG_CASE(NN, VV)                                                                       \
-    case NN * 8 + VV:                                                                         \
-        batched_tile<NN, VV, MODE, Ix>(src, dst, d.dQ, d.T, d.g, item.tile, A, B, dtr, smem_raw); \
-        break;
-        if constexpr (CLASS == 0) {
-            switch (item.code) {
-                DG_FOR_EACH_CODE_C0(DG_CASE)
-            default: break;
-            }
-        } else {
-            switch (item.code) {
-                DG_FOR_EACH_CODE_C1(DG_CASE)
-            default: break;
-            }
-        }
-#undef DG_CASE
-    }
-}
-
-// Lambda of every instance: node speeds of each tile in float, maximum in
-// double (bit patterns of non-negative doubles; NaN above every finite value).
-template <int N, int TX, int TY>
-__device__ __forceinline__ double tile_speed_max(const float *__restrict__ Q, const Geo &g,
-                                                 long long tile, float gamma, bool &bad)
-{
-    const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY;
-    const int bx = (int)(tile % ntx), by = (int)((tile / ntx) % nty);
-    const int bz = (int)(tile / ((long long)ntx * nty));
-    constexpr int N3 = N * N * N;
-    float m = 0.0f;  // float maximum of float speeds; converted once (exact)
-    for (int t = threadIdx.x; t < TX * TY * N3; t += blockDim.x) {
-        const int el = t / N3, node = t - el * N3;
-        const int ex = bx * TX + el % TX, ey = by * TY + el / TX;
-        if (ex >= g.nx || ey >= g.ny) continue;
-        const long long e = ex + (long long)g.nx * (ey + (long long)g.ny * bz);
-        const long long o = e * N3 + node, pl = g.E * N3;
-        float sp;
-        if (!node_speed_f(Q[o], Q[pl + o], Q[2 * pl + o], Q[3 * pl + o], Q[4 * pl + o], gamma, sp)) {
-            bad = true;
-            continue;
-        }
-        m = fmaxf(m, sp);
-    }
-    return (double)m;
-}
-
-static __global__ void __launch_bounds__(512)
-    batched_cfl_kernel(const BatchItem *__restrict__ items, int nitems,
-                       const InstDev *__restrict__ inst, int parity, int *err)
-{
-    __shared__ unsigned long long red[16];
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const BatchItem item = items[it];
-        const InstDev &d = inst[item.inst];
+        const float *Q = parity == 0 ? d.Q : d.Qt;
+        const long long pl = d.g.E * (long long)((d.g.p + 1) * (d.g.p + 1) * (d.g.p + 1));
+        const float gf = (float)d.g.gamma;
+        float mf = 0.0f;
         bool bad = false;
-        double m = 0.0;
-        switch (item.code) {
-#define DG_CASE(NN, VV)                                                                          \
-    case NN * 8 + VV:                                                                            \
-        m = tile_speed_max<NN, TileShape<NN, VV>::TX, TileShape<NN, VV>::TY>(                    \
-            parity == 0 ? d.Q : d.Qt, d.g, item.tile, \
-                                                                              d.T.gamma, bad);    \
-        break;
-            DG_FOR_EACH_CODE(DG_CASE)
-#undef DG_CASE
-        default: break;
+        for (long long t = item.begin + threadIdx.x; t < item.end; t += blockDim.x) {
+            float sp;
+            if (!node_speed_f(Q[t], Q[pl + t], Q[2 * pl + t], Q[3 * pl + t], Q[4 * pl + t], gf, sp)) {
+                bad = true;
+                continue;
+            }
+            mf = fmaxf(mf, sp);
         }
+        double m = (double)mf;
         if (bad) {
             atomicOr(err, 1);
             m = __longlong_as_double(0x7ff8000000000000LL);
         }
+        __shared__ unsigned long long red[8];
         unsigned long long bits = (unsigned long long)__double_as_longlong(m);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {

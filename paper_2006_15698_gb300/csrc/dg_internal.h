@@ -146,39 +146,44 @@ struct InstDev {
     float *Q, *Qt, *dQ;            // state, second state, RK register
     double *dt;                    // this instance's time step (device)
     unsigned long long *lam_bits;  // CFL maximum slot
-    int code;                      // N * 8 + tile variant
 };
 
-// One work item: one tile of one instance.
-struct BatchItem {
+// One work item of a batch's time-step reduction: nodes [begin, end) of one
+// instance (node index within a field plane).
+struct LambdaItem {
     int inst;
-    int code;
-    long long tile;
+    long long begin, end;
 };
+constexpr long long kLambdaNodes = 1 << 14;
+
+// One work item of a batch's line-kernel stage: one (column, z chunk) CTA of
+// one instance (block = column + chunk x columns, as in a single-mesh launch).
+struct LineItem {
+    int inst;
+    int block;
+    int zchunk;
+};
+
+// Cross-section (TX, TY) of the line kernel of order N (false if N unsupported).
+bool line_shape_info(int N, int *tx, int *ty);
+// CTAs of the batched line kernel of order N resident per SM (0 on error).
+int batch_line_blocks_per_sm(int N, bool small);
+// One float-form RK stage of every listed work item (all of order N) of a
+// batch; small: every instance's offsets fit a 32-bit int.
+cudaError_t batch_line_stage(const LineItem *items, int nitems, const InstDev *inst, int N,
+                             int parity, float A, float B, bool small, cudaStream_t s);
 
 // Host-side facts about a tile code (N * 8 + variant): tile shape, threads,
 // dynamic shared memory of the fused stage; false for an unknown code.
 bool tile_code_info(int code, int *tx, int *ty, int *threads, size_t *smem);
 
-// Launchers of the batched kernels (dg_kernels_f32.cu): one persistent launch
-// over all items; `threads` and `smem` cover the largest tile of the batch.
-// size class of a tile code (0: N <= 6, 256 threads; 1: N = 7, 352 threads)
-int batch_code_class(int code);
-int batch_class_threads(int cls);
-// small: every instance's state offsets fit a 32-bit int (cheaper indexing)
-cudaError_t batch_stage(const BatchItem *items, int nitems, const InstDev *inst, int parity,
-                        float A, float B, int cls, bool small, int grid, size_t smem,
-                        cudaStream_t s);
-// parity 0: the current state is in Q, 1: in the second state Qt
-// (nitems may be 0: then only the time steps are finalised from the Lambda
-// slots, which other launches may have filled)
-cudaError_t batch_cfl(const BatchItem *items, int nitems, const InstDev *inst, int ninst,
-                      int parity, double cfl, int *err, int grid, int threads, cudaStream_t s);
-// the same in two halves: Lambda of the items' tiles, then dt of every instance
-cudaError_t batch_lambda(const BatchItem *items, int nitems, const InstDev *inst, int parity,
-                         int *err, int grid, int threads, cudaStream_t s);
+// Launchers of the batched time-step kernels (dg_batch_f32.cu): Lambda of
+// the listed node ranges (parity 0: the current state is in Q, 1: in the
+// second state Qt), then dt of every instance from its Lambda slot (which
+// other launches may have filled).
+cudaError_t batch_lambda(const LambdaItem *items, int nitems, const InstDev *inst, int parity,
+                         int *err, int grid, cudaStream_t s);
 cudaError_t batch_dt(const InstDev *inst, int ninst, double cfl, cudaStream_t s);
-int batch_stage_blocks_per_sm(int cls, bool small, size_t smem);
 
 // Lambda (maximum wave-speed sum) of a float state merged into *lam_bits
 // (no time step yet), and one float-form RK stage of a single mesh

@@ -1209,6 +1209,51 @@ cudaError_t stage_n(const Geo &g, const Ops<real> &T, const real *src, real *dst
     }
 }
 
+// One float-form RK stage (MODE 1) of a batch's work items of order N: one
+// launch of batched_line_kernel, one CTA per item.
+template <int N, typename real>
+cudaError_t batch_line_n(const LineItem *items, int nitems, const InstDev *inst, int parity,
+                         float A, float B, bool small, cudaStream_t s)
+{
+    if constexpr (std::is_same<real, float>::value) {
+        using LS = LineShape<N, 0>;
+        using LT = LineTile<N, LS::TX, LS::TY, LS::NS, LS::RPAD>;
+        if (nitems <= 0) return cudaSuccess;
+        auto kernel = small ? batched_line_kernel<N, 1, int> : batched_line_kernel<N, 1, long long>;
+        if (LT::BYTES > 48 * 1024) {
+            cudaError_t err = cudaFuncSetAttribute(
+                kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LT::BYTES);
+            if (err != cudaSuccess) return err;
+        }
+        kernel<<<(unsigned)nitems, LT::THREADS, LT::BYTES, s>>>(items, inst, parity, A, B);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+// CTAs of batched_line_kernel<N> resident per SM (0 on error)
+template <int N, typename real>
+int batch_line_blocks_per_sm_n(bool small)
+{
+    if constexpr (std::is_same<real, float>::value) {
+        using LS = LineShape<N, 0>;
+        using LT = LineTile<N, LS::TX, LS::TY, LS::NS, LS::RPAD>;
+        auto kernel = small ? batched_line_kernel<N, 1, int> : batched_line_kernel<N, 1, long long>;
+        if (LT::BYTES > 48 * 1024 &&
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)LT::BYTES) != cudaSuccess)
+            return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, LT::THREADS, LT::BYTES) !=
+            cudaSuccess)
+            return 0;
+        return n;
+    } else {
+        return 0;
+    }
+}
+
 // host table of the quadrature weight of every in-element node
 inline NodeWeights node_weights(const Geo &g)
 {
@@ -1370,7 +1415,10 @@ cudaError_t advance_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, doubl
     KW cudaError_t rk_stage_n<NN, REAL>(const Geo &, const Ops<REAL> &, const REAL *, REAL *,  \
                                         REAL *, const double *, int, Work &, cudaStream_t);  \
     KW cudaError_t ztraces_n<NN, REAL>(const Geo &, const Ops<REAL> &, const REAL *, REAL *,   \
-                                       REAL *, cudaStream_t);
+                                       REAL *, cudaStream_t);                                \
+    KW cudaError_t batch_line_n<NN, REAL>(const LineItem *, int, const InstDev *, int, float,  \
+                                          float, bool, cudaStream_t);                        \
+    KW int batch_line_blocks_per_sm_n<NN, REAL>(bool);
 
 template <typename real>
 cudaError_t Launch<real>::rk_stage(const Geo &g, const Ops<real> &T, const real *Qin, real *Qout,

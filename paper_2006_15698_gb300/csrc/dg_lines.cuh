@@ -43,10 +43,13 @@ struct LineShape;
 struct LineDefaults {
     static constexpr bool SWZ = false, UT = false, RC = false, PFN = false;
     static constexpr int NS = 3, RPAD = 0;
+    // resident CTAs per SM the batched kernel must allow (its registers then
+    // match the single-mesh kernel's; 0: no bound)
+    static constexpr int BMINB = 0;
 };
 template <> struct LineShape<1, 0> : LineDefaults { static constexpr int TX = 16, TY = 16, NS = 2, RPAD = 1; };
-template <> struct LineShape<2, 0> : LineDefaults { static constexpr int TX = 8, TY = 8, NS = 2, RPAD = 8; };
-template <> struct LineShape<3, 0> : LineDefaults { static constexpr int TX = 4, TY = 4, NS = 2; };
+template <> struct LineShape<2, 0> : LineDefaults { static constexpr int TX = 8, TY = 8, NS = 2, RPAD = 8, BMINB = 2; };
+template <> struct LineShape<3, 0> : LineDefaults { static constexpr int TX = 4, TY = 4, NS = 2, BMINB = 3; };
 template <> struct LineShape<4, 0> : LineDefaults {
     static constexpr int TX = 2, TY = 2, NS = 2;
     static constexpr bool SWZ = true, UT = true, PFN = true;
@@ -54,7 +57,7 @@ template <> struct LineShape<4, 0> : LineDefaults {
 template <> struct LineShape<5, 0> : LineDefaults { static constexpr int TX = 3, TY = 2, NS = 2; };
 template <> struct LineShape<6, 0> : LineDefaults {
     static constexpr int TX = 3, TY = 1;
-    static constexpr bool UT = true;
+    static constexpr bool UT = true, RC = true;
 };
 template <> struct LineShape<7, 0> : LineDefaults {
     static constexpr int TX = 2, TY = 1;
@@ -142,16 +145,16 @@ __device__ __forceinline__ void slot_interface(const float *__restrict__ Qin, co
     }
 }
 
-// One column chunk of the stage; MODE and Ix as for column_stage_kernel.
-// Launched with exactly LineTile::THREADS threads (launch_column_ix): the
-// copy offsets and the interface-task loop stride assume that block size.
+// One column chunk of the stage, block = column + chunk x columns of the mesh
+// (the CTA's index in a launch over one mesh); MODE and Ix as for
+// column_stage_kernel.  Run by exactly LineTile::THREADS threads: the copy
+// offsets and the interface-task loop stride assume that block size.
 template <int N, int V, int MODE, typename Ix>
-__global__ void __launch_bounds__(
-    LineTile<N, LineShape<N, V>::TX, LineShape<N, V>::TY, LineShape<N, V>::NS,
-             LineShape<N, V>::RPAD>::THREADS)
-    line_stage_kernel(const float *__restrict__ Qin, float *__restrict__ Out,
-                      float *__restrict__ dQ, const Ops<float> T, const Geo g, float A, float B,
-                      const double *__restrict__ dt, int zchunk)
+__device__ __forceinline__ void line_stage_body(const float *__restrict__ Qin,
+                                                float *__restrict__ Out, float *__restrict__ dQ,
+                                                const Ops<float> &T, const Geo &g, float A,
+                                                float B, const double *__restrict__ dt, int zchunk,
+                                                unsigned block)
 {
     constexpr int TX = LineShape<N, V>::TX, TY = LineShape<N, V>::TY;
     constexpr bool SWZ = LineShape<N, V>::SWZ;
@@ -168,8 +171,8 @@ __global__ void __launch_bounds__(
     float *sOp = sH + LT::HREG;                    // D[3][N][N], Lm[3][N], Lp[3][N], lm[N], lp[N]
 
     const int ncx = (g.nx + TX - 1) / TX, ncy = (g.ny + TY - 1) / TY;
-    const int col = (int)(blockIdx.x % (unsigned)(ncx * ncy));
-    const int chunk = (int)(blockIdx.x / (unsigned)(ncx * ncy));
+    const int col = (int)(block % (unsigned)(ncx * ncy));
+    const int chunk = (int)(block / (unsigned)(ncx * ncy));
     const int ex0 = (col % ncx) * TX, ey0 = (col / ncx) * TY;
     const int txv = min(TX, g.nx - ex0), tyv = min(TY, g.ny - ey0);
     const int z0 = chunk * zchunk;
@@ -482,4 +485,39 @@ __global__ void __launch_bounds__(
         if constexpr (NS == 3)
             if (z + 3 <= z1) prefetch(z + 3);
     }
+}
+
+// The stage over one mesh: one CTA per (column, z chunk).
+template <int N, int V, int MODE, typename Ix>
+__global__ void __launch_bounds__(
+    LineTile<N, LineShape<N, V>::TX, LineShape<N, V>::TY, LineShape<N, V>::NS,
+             LineShape<N, V>::RPAD>::THREADS)
+    line_stage_kernel(const float *__restrict__ Qin, float *__restrict__ Out,
+                      float *__restrict__ dQ, const Ops<float> T, const Geo g, float A, float B,
+                      const double *__restrict__ dt, int zchunk)
+{
+    line_stage_body<N, V, MODE, Ix>(Qin, Out, dQ, T, g, A, B, dt, zchunk, blockIdx.x);
+}
+
+// The stage over the instances of one degree of a batch: one CTA per work
+// item (instance, column, z chunk), the same body as line_stage_kernel, so
+// an instance's floats are those of the same mesh stepped alone.  parity 0:
+// the stage reads Q and writes the second state Qt; 1: the reverse.
+template <int N, int MODE, typename Ix>
+__global__ void __launch_bounds__(
+    LineTile<N, LineShape<N, 0>::TX, LineShape<N, 0>::TY, LineShape<N, 0>::NS,
+             LineShape<N, 0>::RPAD>::THREADS, LineShape<N, 0>::BMINB)
+    batched_line_kernel(const LineItem *__restrict__ items, const InstDev *__restrict__ inst,
+                        int parity, float A, float B)
+{
+    // the instance's geometry staged in shared memory: the body reads it
+    // where the single-mesh kernel reads its parameter bank, without holding
+    // it in registers
+    __shared__ Geo sg;
+    const LineItem it = items[blockIdx.x];
+    const InstDev *I = inst + it.inst;
+    if (threadIdx.x == 0) sg = I->g;
+    __syncthreads();
+    line_stage_body<N, 0, MODE, Ix>(parity ? I->Qt : I->Q, parity ? I->Q : I->Qt, I->dQ, I->T, sg,
+                                    A, B, I->dt, it.zchunk, (unsigned)it.block);
 }

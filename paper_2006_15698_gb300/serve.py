@@ -96,6 +96,9 @@ class Report:
     peak_active: int
     iterations: int
     rebuilds: int
+    rebuild_s: float = 0.0   # host time spent rebuilding the batch
+    enqueue_s: float = 0.0   # host time spent enqueueing steps
+    wait_s: float = 0.0      # host time spent waiting for steps to finish
 
     def percentile(self, q):
         lat = sorted(o.latency for o in self.outcomes)
@@ -110,7 +113,8 @@ class Report:
                 "requests_per_s": len(self.outcomes) / self.wall if self.wall else None,
                 "p50_s": self.percentile(50), "p99_s": self.percentile(99),
                 "peak_bytes": self.peak_bytes, "peak_active": self.peak_active,
-                "iterations": self.iterations, "batch_rebuilds": self.rebuilds}
+                "iterations": self.iterations, "batch_rebuilds": self.rebuilds,
+                "rebuild_s": self.rebuild_s, "enqueue_s": self.enqueue_s, "wait_s": self.wait_s}
 
 
 class TimeoutError_(RuntimeError):
@@ -136,7 +140,7 @@ class Server:
         waiting, active = [], []      # active: [request, remaining steps, admit time]
         outcomes = []
         used = peak = peak_active = iters = rebuilds = 0
-        dof_stage = 0.0
+        dof_stage = rebuild_s = enqueue_s = wait_s = 0.0
         t0 = self.clock()
         changed = False
         i = 0
@@ -159,13 +163,19 @@ class Server:
                     self.ex.idle_until(t0 + pending[i].arrival, self.clock)
                 continue
             if changed:
+                tr = self.clock()
                 self.ex.rebuild([a[0] for a in active])
+                rebuild_s += self.clock() - tr
                 rebuilds += 1
                 changed = False
             k = 2 if all(a[1] >= 2 for a in active) else 1
+            tr = self.clock()
             self.ex.step(k)
+            tw = self.clock()
+            enqueue_s += tw - tr
             if not self.ex.wait(self.deadline):
                 raise TimeoutError_(f"step did not finish within {self.deadline} s")
+            wait_s += self.clock() - tw
             iters += 1
             done_t = self.clock() - t0
             still = []
@@ -183,7 +193,7 @@ class Server:
             active = still
         wall = self.clock() - t0
         return Report(sorted(outcomes, key=lambda o: o.rid), wall, dof_stage, peak, peak_active,
-                      iters, rebuilds)
+                      iters, rebuilds, rebuild_s, enqueue_s, wait_s)
 
 
 class GpuExecutor:

@@ -1,17 +1,17 @@
 """Tile variants of the float form's fused stage, and batches of independent
-float meshes (one persistent launch per RK stage for the small instances,
-own launches on the batch's streams for the others, optional CUDA graph).
-The batch tests run with every instance in the persistent launch, with the
-default split and with every instance on its own launches
-(dg_set_batch_direct_nodes).  (Single meshes default to the line stage
-kernel; the tests that compare a single mesh with a batch bitwise select the
-tile kernel for it.)
+float meshes (the shared instances: one launch per RK stage and degree of the
+line kernel over work items (instance, column, z chunk); the others on own
+launches on the batch's streams; optional CUDA graph).  The batch tests run
+with every instance shared, with the default split and with every instance
+on its own launches (dg_set_batch_direct_nodes).  (The tests that compare a
+single mesh with a batch bitwise select the line kernel for it, which the
+shared launches run.)
 
 * every tile variant of every degree gives the oracle's right-hand side
   (FP32 tolerance), also on meshes that tiles cover raggedly;
 * an instance advanced inside a batch equals the same instance advanced
-  alone, bitwise (same tile code, same arithmetic), and its time step equals
-  dg_cfl_dt's;
+  alone, bitwise (the same line-kernel body, the same arithmetic), and its
+  time step equals dg_cfl_dt's;
 * graph-replayed steps equal directly launched steps bitwise.
 """
 import math
@@ -85,8 +85,8 @@ def test_batch_matches_single_meshes(dgm, use_graph, direct):
     dg = dgm
     import torch
     _set_direct(dg, direct)
-    for p in range(0, 7):  # single meshes on the batch's tile kernel: bitwise comparable
-        dg.dg_set_stage_kernel(p, dg.DG_STAGE_TILE)
+    for p in range(0, 7):  # single meshes on the batch's line kernel: bitwise comparable
+        dg.dg_set_stage_kernel(p, dg.DG_STAGE_LINES)
     specs = _specs(11, 7)
     batch = dg.Batch(specs)
     for i, s in enumerate(specs):
@@ -195,12 +195,12 @@ def test_hybrid_batch_large_instances_match_single_meshes(dgm, kernel):
     dg = dgm
     import torch
     # the large instances' degrees (3, 4) run the kernel under test; the small
-    # instances (degrees 2, 5) share the batched tile launch, so their single
-    # meshes use the tile kernel too
+    # instances (degrees 2, 5) share the batched line-kernel launches, so their
+    # single meshes use the line kernel
     dg.dg_set_batch_direct_nodes(1 << 19)
     for p in range(0, 7):
         big = p in (3, 4)
-        dg.dg_set_stage_kernel(p, dg.STAGE_KINDS[kernel] if big else dg.DG_STAGE_TILE)
+        dg.dg_set_stage_kernel(p, dg.STAGE_KINDS[kernel] if big else dg.DG_STAGE_LINES)
     specs = [dict(nx=24, ny=24, nz=24, p=3, Lx=10.0, Ly=10.0, Lz=10.0),   # 884,736 nodes: own launches
              dict(nx=5, ny=6, nz=5, p=2, Lx=10.0, Ly=10.0, Lz=10.0),
              dict(nx=12, ny=10, nz=9, p=5, Lx=10.0, Ly=10.0, Lz=10.0),    # 233,280 nodes: shared
@@ -218,6 +218,47 @@ def test_hybrid_batch_large_instances_match_single_meshes(dgm, kernel):
     with torch.cuda.stream(stream):
         for use_graph in (False, True, True):
             batch.step(0.5, use_graph=use_graph)
+            for m, Q, dQ, dt in singles:
+                m.cfl_dt(Q, 0.5, dt)
+                m.rk_step(Q, dQ, dt)
+    torch.cuda.synchronize()
+    dts = batch.dts()
+    for i, (m, Q, dQ, dt) in enumerate(singles):
+        assert dts[i] == float(dt.item()), i
+        assert torch.equal(batch.Q[i], Q), (i, specs[i])
+    assert batch.last_error() == dg.DG_OK
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_shared_launch_every_degree_matches_single_meshes(dgm, use_graph):
+    # every instance in the shared line-kernel launches, degrees 0..6 (ragged
+    # columns, z chunks), each equal to the same mesh stepped alone
+    dg = dgm
+    import torch
+    dg.dg_set_batch_direct_nodes(dg.BATCH_NEVER_DIRECT)
+    for p in range(0, 7):
+        dg.dg_set_stage_kernel(p, dg.DG_STAGE_LINES)
+    specs = [dict(nx=5, ny=4, nz=19, p=0, Lx=10.0, Ly=10.0, Lz=10.0),
+             dict(nx=9, ny=3, nz=2, p=1, Lx=10.0, Ly=10.0, Lz=10.0),
+             dict(nx=4, ny=5, nz=9, p=2, Lx=10.0, Ly=10.0, Lz=10.0),
+             dict(nx=3, ny=5, nz=17, p=3, Lx=10.0, Ly=10.0, Lz=10.0),
+             dict(nx=3, ny=2, nz=3, p=4, Lx=10.0, Ly=10.0, Lz=10.0),
+             dict(nx=4, ny=1, nz=10, p=5, Lx=10.0, Ly=10.0, Lz=10.0),
+             dict(nx=3, ny=2, nz=1, p=6, Lx=10.0, Ly=10.0, Lz=10.0)]
+    batch = dg.Batch(specs)
+    assert batch.n_items > 0
+    for i in range(len(specs)):
+        batch.init(i, "vortex", inputs.vortex_params(300 + i, BOX))
+    singles = []
+    for i, sp in enumerate(specs):
+        m = dg.Mesh(sp["nx"], sp["ny"], sp["nz"], sp["p"], *BOX, precision=dg.DG_FP32)
+        Q = batch.Q[i].clone()
+        singles.append((m, Q, torch.zeros_like(Q), torch.zeros(1, dtype=torch.float64, device="cuda")))
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch.step(0.5, nsteps=3, use_graph=use_graph)
+        for _ in range(3):
             for m, Q, dQ, dt in singles:
                 m.cfl_dt(Q, 0.5, dt)
                 m.rk_step(Q, dQ, dt)
