@@ -58,6 +58,9 @@ WORKLOADS = {
     "vortex64_p3_fp32": dict(nel=(64, 64, 64), p=3, box=(0, 0, 0, 16.0, 16.0, 16.0),
                              init="vortex", params=None, prec="fp32", cfl=0.5,
                              desc="isentropic vortex (seed 0), 16^3 box, 64^3 elements, p=3, FP32"),
+    "tgv32_p4_fp32": dict(nel=(32, 32, 32), p=4, box=(0, 0, 0, TWO_PI, TWO_PI, TWO_PI),
+                          init="tgv", params=[1.0, 1.0, 0.1], prec="fp32", cfl=0.5,
+                          desc="Taylor-Green vortex, 32^3 elements, p=4, FP32"),
     "vortex48_p4_fp32": dict(nel=(48, 48, 48), p=4, box=(0, 0, 0, 16.0, 16.0, 16.0),
                              init="vortex", params=None, prec="fp32", cfl=0.5,
                              desc="isentropic vortex (seed 0), 16^3 box, 48^3 elements, p=4, FP32"),
