@@ -344,6 +344,16 @@ typedef struct {
 typedef struct dg_batch dg_batch;
 dg_status dg_batch_create(int n, const dg_instance *instances, dg_batch **out);
 void dg_batch_destroy(dg_batch *batch);
+/* Replace a batch's instance list by a new one (any n, sizes and degrees:
+ * requests joining and leaving a serving loop), as if the batch had been
+ * created for it, keeping its device arrays and streams where they are large
+ * enough (no allocation, free or device-wide synchronisation when they are;
+ * second states the batch allocated for the old list are freed).  Recorded
+ * graphs are dropped and recorded again at the next graph step.  The batch
+ * must be idle: every step enqueued on it has completed (the new
+ * descriptors are copied over the old ones).  Errors as dg_batch_create; on
+ * an error the batch holds no instances until a successful update. */
+dg_status dg_batch_update(dg_batch *batch, int n, const dg_instance *instances);
 dg_status dg_set_batch_direct_nodes(int64_t nodes);
 int64_t dg_get_batch_direct_nodes(void);
 dg_status dg_batch_sizes(const dg_batch *batch, int64_t *n_dof, int64_t *n_items);

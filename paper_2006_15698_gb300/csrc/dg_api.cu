@@ -577,6 +577,9 @@ struct dg_batch {
     double *d_partials = nullptr;
     std::vector<void *> qt;             // second states owned by the batch
     int grid = 1;                   // CTAs of the time-step launch
+    // capacities of the reusable device arrays (dg_batch_update): d_dt, d_lam,
+    // d_inst (elements); d_items; d_litems
+    size_t cap_inst[3] = {0, 0, 0}, cap_items = 0, cap_litems = 0;
     bool small = true;              // every instance's offsets fit a 32-bit int
     std::vector<int> direct;        // large instances: launched by themselves
     // streams the large instances' stage launches run on, concurrently with
@@ -698,10 +701,12 @@ cudaError_t batch_enqueue(const dg_batch *b, double cfl, int nsteps, cudaStream_
 
 extern "C" {
 
-dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
+}  // extern "C"
+
+namespace {
+
+dg_status check_instances(int n, const dg_instance *desc)
 {
-    if (!out) return DG_ERR_ARG;
-    *out = nullptr;
     if (n < 1 || !desc) return DG_ERR_ARG;
     for (int i = 0; i < n; ++i) {
         const dg_instance &d = desc[i];
@@ -715,11 +720,47 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
         const long long E = (long long)d.nx * d.ny * d.nz;
         if (E * (d.p + 1) * (d.p + 1) * (d.p + 1) >= (1LL << 40)) return DG_ERR_ARG;
     }
-    dg_batch *b = new (std::nothrow) dg_batch();
-    if (!b) return DG_ERR_OOM;
+    return DG_OK;
+}
+
+// a device array of at least `need` elements, reallocated (grown by half)
+// only when the current one is too small
+template <typename T>
+cudaError_t ensure(T **p, size_t *cap, size_t need)
+{
+    if (need <= *cap) return cudaSuccess;
+    const size_t c = std::max(need, *cap + *cap / 2);
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc((void **)p, c * sizeof(T));
+    if (e == cudaSuccess) *cap = c;
+    return e;
+}
+
+// (Re)build the batch for the instance list desc (validated): descriptors,
+// work lists, lanes; device buffers and streams of an earlier list are
+// reused where large enough.  Recorded graphs are dropped.
+dg_status batch_assign(dg_batch *b, int n, const dg_instance *desc)
+{
+    for (int k = 1; k <= 2; ++k) {
+        if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+        b->exec[k] = nullptr;
+        b->graph_cfl[k] = -1.0;
+    }
+    for (void *p : b->qt) cudaFree(p);
+    b->qt.clear();
     const long long direct_nodes = g_direct_nodes.load();
     b->n = n;
-    b->inst.resize(n);
+    b->inst.assign(n, dg::InstDev{});
+    b->dofs.clear();
+    b->direct.clear();
+    b->items.clear();
+    b->litems.clear();
+    b->lane_of.clear();
+    b->small = true;
+    b->nlanes = 0;
+    for (int N = 0; N <= dg::NMAX; ++N) b->lbeg[N] = b->lend[N] = b->group_lane[N] = 0;
     cudaError_t err = cudaSuccess;
     for (int i = 0; i < n && err == cudaSuccess; ++i) {
         const dg_instance &d = desc[i];
@@ -755,19 +796,11 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
         b->dofs.push_back(g.E * N * N * N);
         if ((long long)dg::NF * g.E * N * N * N > 0x7fffffffLL) b->small = false;
     }
-    if (err == cudaSuccess) err = cudaMalloc((void **)&b->d_dt, sizeof(double) * n);
-    if (err == cudaSuccess) err = cudaMalloc((void **)&b->d_lam, sizeof(unsigned long long) * n);
-    if (err == cudaSuccess) err = cudaMalloc((void **)&b->d_err, sizeof(int));
-    if (err == cudaSuccess)
-        err = cudaMalloc((void **)&b->d_partials, (size_t)dg::kNormBlocks * 8 * sizeof(double));
+    if (err == cudaSuccess) err = ensure(&b->d_dt, &b->cap_inst[0], (size_t)n);
+    if (err == cudaSuccess) err = ensure(&b->d_lam, &b->cap_inst[1], (size_t)n);
+    if (err == cudaSuccess) err = ensure(&b->d_inst, &b->cap_inst[2], (size_t)n);
     if (err == cudaSuccess) err = cudaMemset(b->d_lam, 0, sizeof(unsigned long long) * n);
-    if (err == cudaSuccess) err = cudaMemset(b->d_err, 0, sizeof(int));
-    if (err != cudaSuccess) {
-        dg_status st = cuda_status(err);
-        cudaGetLastError();
-        batch_free(b);
-        return st;
-    }
+    if (err != cudaSuccess) return cuda_status(err);
     // time-step work list: every shared instance's nodes in ranges of at
     // most kLambdaNodes
     for (int i = 0; i < n; ++i) {
@@ -781,67 +814,53 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
         for (long long t = 0; t < b->dofs[i]; t += dg::kLambdaNodes)
             b->items.push_back({i, t, std::min(b->dofs[i], t + dg::kLambdaNodes)});
         int lx, ly;
-        if (!dg::line_shape_info(I.g.p + 1, &lx, &ly)) {
-            batch_free(b);
-            return DG_ERR_UNSUPPORTED;
-        }
+        if (!dg::line_shape_info(I.g.p + 1, &lx, &ly)) return DG_ERR_UNSUPPORTED;
     }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // stage work items: the line kernel's columns of the shared instances,
     // each cut into z chunks.  Per order N one chunk length for all its
     // instances, chosen as a single mesh's launch chooses it: the length that
     // minimises (waves of the GPU's resident CTAs) x (layers per chunk + the
     // chunk's extra prologue layer) over the order's columns.
-    {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        for (int N = 1; N <= dg::NMAX; ++N) {
-            std::vector<int> members;
-            int maxz = 0;
-            for (int i = 0; i < n; ++i)
-                if (b->inst[i].g.p + 1 == N && b->dofs[i] < direct_nodes) {
-                    members.push_back(i);
-                    maxz = std::max(maxz, b->inst[i].g.nz);
-                }
-            if (members.empty()) continue;
-            int lx, ly;
-            dg::line_shape_info(N, &lx, &ly);
-            const int per_sm = dg::batch_line_blocks_per_sm(N, b->small);
-            const long long resident = (long long)std::max(1, sms) * std::max(1, per_sm);
-            auto ncols = [&](int i) {
-                const dg::Geo &g = b->inst[i].g;
-                return (long long)((g.nx + lx - 1) / lx) * ((g.ny + ly - 1) / ly);
-            };
-            int best_zc = maxz;
-            double best = -1.0;
-            for (int zc = 1; zc <= maxz; ++zc) {
-                long long ctas = 0;
-                for (int i : members) ctas += ncols(i) * ((b->inst[i].g.nz + zc - 1) / zc);
-                const double cost = (double)((ctas + resident - 1) / resident) * (zc + 1);
-                if (best < 0.0 || cost < best) { best = cost; best_zc = zc; }
+    for (int N = 1; N <= dg::NMAX; ++N) {
+        std::vector<int> members;
+        int maxz = 0;
+        for (int i = 0; i < n; ++i)
+            if (b->inst[i].g.p + 1 == N && b->dofs[i] < direct_nodes) {
+                members.push_back(i);
+                maxz = std::max(maxz, b->inst[i].g.nz);
             }
-            b->lbeg[N] = (int)b->litems.size();
-            for (int i : members) {
-                const int zc = std::min(best_zc, b->inst[i].g.nz);
-                const long long nblk = ncols(i) * ((b->inst[i].g.nz + zc - 1) / zc);
-                if (nblk > 0x7fffffffLL) {
-                    batch_free(b);
-                    return DG_ERR_ARG;
-                }
-                for (long long k = 0; k < nblk; ++k) b->litems.push_back({i, (int)k, zc});
-            }
-            b->lend[N] = (int)b->litems.size();
+        if (members.empty()) continue;
+        int lx, ly;
+        dg::line_shape_info(N, &lx, &ly);
+        const int per_sm = dg::batch_line_blocks_per_sm(N, b->small);
+        const long long resident = (long long)std::max(1, sms) * std::max(1, per_sm);
+        auto ncols = [&](int i) {
+            const dg::Geo &g = b->inst[i].g;
+            return (long long)((g.nx + lx - 1) / lx) * ((g.ny + ly - 1) / ly);
+        };
+        int best_zc = maxz;
+        double best = -1.0;
+        for (int zc = 1; zc <= maxz; ++zc) {
+            long long ctas = 0;
+            for (int i : members) ctas += ncols(i) * ((b->inst[i].g.nz + zc - 1) / zc);
+            const double cost = (double)((ctas + resident - 1) / resident) * (zc + 1);
+            if (best < 0.0 || cost < best) { best = cost; best_zc = zc; }
         }
+        b->lbeg[N] = (int)b->litems.size();
+        for (int i : members) {
+            const int zc = std::min(best_zc, b->inst[i].g.nz);
+            const long long nblk = ncols(i) * ((b->inst[i].g.nz + zc - 1) / zc);
+            if (nblk > 0x7fffffffLL) return DG_ERR_ARG;
+            for (long long k = 0; k < nblk; ++k) b->litems.push_back({i, (int)k, zc});
+        }
+        b->lend[N] = (int)b->litems.size();
     }
-    if (b->litems.size() > 0x7fffffffULL || b->items.size() > 0x7fffffffULL) {
-        batch_free(b);
-        return DG_ERR_ARG;
-    }
-    err = cudaMalloc((void **)&b->d_inst, sizeof(dg::InstDev) * n);
-    if (err == cudaSuccess && !b->items.empty())
-        err = cudaMalloc((void **)&b->d_items, sizeof(dg::LambdaItem) * b->items.size());
-    if (err == cudaSuccess && !b->litems.empty())
-        err = cudaMalloc((void **)&b->d_litems, sizeof(dg::LineItem) * b->litems.size());
+    if (b->litems.size() > 0x7fffffffULL || b->items.size() > 0x7fffffffULL) return DG_ERR_ARG;
+    err = ensure(&b->d_items, &b->cap_items, b->items.size());
+    if (err == cudaSuccess) err = ensure(&b->d_litems, &b->cap_litems, b->litems.size());
     if (err == cudaSuccess)
         err = cudaMemcpy(b->d_inst, b->inst.data(), sizeof(dg::InstDev) * n, cudaMemcpyHostToDevice);
     if (err == cudaSuccess && !b->items.empty())
@@ -850,16 +869,8 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
     if (err == cudaSuccess && !b->litems.empty())
         err = cudaMemcpy(b->d_litems, b->litems.data(), sizeof(dg::LineItem) * b->litems.size(),
                          cudaMemcpyHostToDevice);
-    if (err != cudaSuccess) {
-        dg_status st = cuda_status(err);
-        cudaGetLastError();
-        batch_free(b);
-        return st;
-    }
-    // grid of the time-step reduction over the tiles: as many CTAs as fit
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return cuda_status(err);
+    // grid of the time-step reduction: as many CTAs as fit
     const int ni = (int)b->items.size();
     b->grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * 8, (long long)ni));
     // lanes: the units of stage work -- each large instance, and the shared
@@ -875,8 +886,7 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
         if (b->lend[N] <= b->lbeg[N]) continue;
         long long d = 0;
         for (int i = 0; i < n; ++i)
-            if (b->inst[i].g.p + 1 == N && std::find(b->direct.begin(), b->direct.end(), i) == b->direct.end())
-                d += b->dofs[i];
+            if (b->inst[i].g.p + 1 == N && b->dofs[i] < direct_nodes) d += b->dofs[i];
         unit_dof.push_back(d);
         unit_N.push_back(N);
     }
@@ -894,20 +904,51 @@ dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
             else b->group_lane[unit_N[k]] = l;
             load[l] += unit_dof[k];
         }
-        err = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+        if (!b->fork_ev) err = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
         for (int l = 0; l < b->nlanes && err == cudaSuccess; ++l) {
+            if (b->lane[l]) continue;  // made for an earlier list
             err = cudaStreamCreateWithFlags(&b->lane[l], cudaStreamNonBlocking);
             if (err == cudaSuccess) err = cudaEventCreateWithFlags(&b->join_ev[l], cudaEventDisableTiming);
         }
-        if (err != cudaSuccess) {
-            dg_status st = cuda_status(err);
-            cudaGetLastError();
-            batch_free(b);
-            return st;
-        }
+        if (err != cudaSuccess) return cuda_status(err);
+    }
+    return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_batch_create(int n, const dg_instance *desc, dg_batch **out)
+{
+    if (!out) return DG_ERR_ARG;
+    *out = nullptr;
+    dg_status st = check_instances(n, desc);
+    if (st != DG_OK) return st;
+    dg_batch *b = new (std::nothrow) dg_batch();
+    if (!b) return DG_ERR_OOM;
+    cudaError_t err = cudaMalloc((void **)&b->d_err, sizeof(int));
+    if (err == cudaSuccess)
+        err = cudaMalloc((void **)&b->d_partials, (size_t)dg::kNormBlocks * 8 * sizeof(double));
+    if (err == cudaSuccess) err = cudaMemset(b->d_err, 0, sizeof(int));
+    st = err == cudaSuccess ? batch_assign(b, n, desc) : cuda_status(err);
+    if (st != DG_OK) {
+        cudaGetLastError();  // clear a sticky allocation error
+        batch_free(b);
+        return st;
     }
     *out = b;
     return DG_OK;
+}
+
+dg_status dg_batch_update(dg_batch *b, int n, const dg_instance *desc)
+{
+    if (!b) return DG_ERR_ARG;
+    dg_status st = check_instances(n, desc);
+    if (st != DG_OK) return st;
+    st = batch_assign(b, n, desc);
+    if (st != DG_OK) cudaGetLastError();
+    return st;
 }
 
 void dg_batch_destroy(dg_batch *b) { batch_free(b); }

@@ -102,6 +102,8 @@ _lib.dg_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(DgInstance), ctype
 _lib.dg_batch_create.restype = ctypes.c_int
 _lib.dg_batch_destroy.argtypes = [_vp]
 _lib.dg_batch_destroy.restype = None
+_lib.dg_batch_update.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(DgInstance)]
+_lib.dg_batch_update.restype = ctypes.c_int
 _lib.dg_set_batch_direct_nodes.argtypes = [ctypes.c_int64]
 _lib.dg_set_batch_direct_nodes.restype = ctypes.c_int
 _lib.dg_get_batch_direct_nodes.argtypes = []
@@ -506,6 +508,27 @@ class Batch:
 
     def __init__(self, specs, device=None):
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        arr = self._instances(specs)
+        h = _vp()
+        with torch.cuda.device(self.device):
+            _check(_lib.dg_batch_create(len(specs), arr, ctypes.byref(h)), "dg_batch_create")
+        self.h = h
+        self._sizes()
+
+    def update(self, specs):
+        """Replace the instance list in place (dg_batch_update); the batch must
+        be idle (its enqueued steps complete)."""
+        arr = self._instances(specs)
+        with torch.cuda.device(self.device):
+            _check(_lib.dg_batch_update(self.h, len(specs), arr), "dg_batch_update")
+        self._sizes()
+
+    def _sizes(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.dg_batch_sizes(self.h, ctypes.byref(a), ctypes.byref(b)), "dg_batch_sizes")
+        self.n_dof, self.n_items = a.value, b.value
+
+    def _instances(self, specs):
         self.specs = [dict(s) for s in specs]
         self.Q, self.dQ, self.Qt = [], [], []
         arr = (DgInstance * len(specs))()
@@ -524,13 +547,7 @@ class Batch:
                                 s.get("z0", 0.0), s.get("Lx", 1.0), s.get("Ly", 1.0), s.get("Lz", 1.0),
                                 s.get("gamma", 1.4), q.data_ptr(), dq.data_ptr(),
                                 None if qt is None else qt.data_ptr())
-        h = _vp()
-        with torch.cuda.device(self.device):
-            _check(_lib.dg_batch_create(len(specs), arr, ctypes.byref(h)), "dg_batch_create")
-        self.h = h
-        a, b = ctypes.c_int64(), ctypes.c_int64()
-        _check(_lib.dg_batch_sizes(h, ctypes.byref(a), ctypes.byref(b)), "dg_batch_sizes")
-        self.n_dof, self.n_items = a.value, b.value
+        return arr
 
     def __len__(self):
         return len(self.specs)

@@ -225,9 +225,13 @@ class GpuExecutor:
         self.handles[q.rid] = h
 
     def rebuild(self, reqs):
+        """The active set changed (between steps, the GPU idle): each CFL
+        group's batch takes its new instance list in place (dg_batch_update:
+        its device arrays and streams are kept), a new group gets a batch."""
         by_cfl = {}
         for q in reqs:
             by_cfl.setdefault(float(q.cfl), []).append(q)
+        old = {cfl: batch for cfl, batch, _ in self.groups}
         with self.torch.cuda.stream(self.stream):
             self.groups = []
             self.where = {}
@@ -239,7 +243,11 @@ class GpuExecutor:
                     s = q.spec()
                     s.update(Q=h["Q"], dQ=h["dQ"], Qt=h["Qt"])
                     specs.append(s)
-                batch = self.dg.Batch(specs)
+                batch = old.pop(cfl, None)
+                if batch is None:
+                    batch = self.dg.Batch(specs)
+                else:
+                    batch.update(specs)
                 for idx, q in enumerate(members):
                     h = self.handles[q.rid]
                     if h["fresh"]:

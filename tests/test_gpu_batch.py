@@ -268,3 +268,52 @@ def test_shared_launch_every_degree_matches_single_meshes(dgm, use_graph):
         assert dts[i] == float(dt.item()), i
         assert torch.equal(batch.Q[i], Q), (i, specs[i])
     assert batch.last_error() == dg.DG_OK
+
+
+@pytest.mark.parametrize("direct", ["never", "default"])
+def test_batch_update_equals_single_meshes(dgm, direct):
+    """dg_batch_update replaces the instance list in place (requests joining
+    and leaving): after updates that shrink, grow (beyond the batch's array
+    capacities) and reorder the list, every instance still steps exactly as
+    the same mesh alone."""
+    dg = dgm
+    import torch
+    _set_direct(dg, direct)
+    for p in range(0, 7):
+        dg.dg_set_stage_kernel(p, dg.DG_STAGE_LINES)
+    pool = _specs(21, 9) + [dict(nx=12, ny=10, nz=9, p=5, Lx=10.0, Ly=10.0, Lz=10.0)]
+    tensors = []
+    for i, sp in enumerate(pool):
+        N = sp["p"] + 1
+        shape = (5, sp["nx"] * sp["ny"] * sp["nz"], N, N, N)
+        tensors.append(dict(Q=torch.empty(shape, dtype=torch.float32, device="cuda"),
+                            dQ=torch.zeros(shape, dtype=torch.float32, device="cuda"),
+                            Qt=torch.empty(shape, dtype=torch.float32, device="cuda")))
+    singles = []
+    for i, sp in enumerate(pool):
+        m = dg.Mesh(sp["nx"], sp["ny"], sp["nz"], sp["p"], *BOX, precision=dg.DG_FP32)
+        Q = m.init("vortex", inputs.vortex_params(400 + i, BOX))
+        tensors[i]["Q"].copy_(Q)
+        singles.append((m, Q, torch.zeros_like(Q), torch.zeros(1, dtype=torch.float64, device="cuda")))
+    lists = [[0, 1, 2], [2, 0], [3, 9, 4, 5, 6, 7, 8, 1], [8, 2]]
+    stream = torch.cuda.Stream()
+    batch = None
+    for members in lists:
+        specs = [dict(pool[i], **tensors[i]) for i in members]
+        if batch is None:
+            batch = dg.Batch(specs)
+        else:
+            batch.update(specs)
+        with torch.cuda.stream(stream):
+            batch.step(0.5, nsteps=2, use_graph=True)
+            for i in members:
+                m, Q, dQ, dt = singles[i]
+                for _ in range(2):
+                    m.cfl_dt(Q, 0.5, dt)
+                    m.rk_step(Q, dQ, dt)
+        torch.cuda.synchronize()
+        dts = batch.dts()
+        for k, i in enumerate(members):
+            assert dts[k] == float(singles[i][3].item()), (members, i)
+            assert torch.equal(tensors[i]["Q"], singles[i][1]), (members, i)
+    assert batch.last_error() == dg.DG_OK

@@ -15,10 +15,14 @@ def test_alone_equals_in_the_mix():
     import torch
     reqs = serve.make_requests(5, 10, 200.0, nrange=(3, 7), prange=(1, 6), steps_range=(3, 7),
                                L=10.0)
+    # all present at once; the byte budget holds about four, so the others
+    # join as earlier ones leave (continuous batching, independent of timing)
+    for q in reqs:
+        q.arrival = 0.0
     budget = 4 * max(q.device_bytes() for q in reqs)
     mix = serve.Server(serve.GpuExecutor(), budget, keep_states=True).run(reqs)
     assert len(mix.outcomes) == len(reqs) and mix.peak_bytes <= budget
-    assert mix.peak_active >= 2
+    assert mix.peak_active >= 2 and mix.rebuilds >= 3
     for q in reqs[:4] + reqs[-2:]:
         alone = serve.Server(serve.GpuExecutor(), budget, keep_states=True).run(
             [serve.Request(q.rid, 0.0, q.n, q.p, q.kind, q.nsteps, q.L, q.cfl, q.params)])
