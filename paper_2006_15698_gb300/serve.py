@@ -5,14 +5,16 @@ Taylor-Green initial state, a number of LSERK45 steps) arrive over time.  The
 server admits waiting requests first-come first-served while their device
 memory (state, RK register, second state: three float state arrays) fits a
 byte budget, keeps every admitted state resident on the GPU, and advances all
-active requests together: between steps it rebuilds the batch when requests
-joined or finished, then replays the batch's recorded step graph (one
-persistent launch per RK stage over every tile of every active request).  A
+active requests together: between steps it gives the batch the new active set when requests joined or
+finished, then replays the batch's recorded step graph; while the active set
+cannot change it keeps a second step enqueued behind the one in flight, so
+the GPU does not idle during the host's bookkeeping.  A
 request completes after exactly its number of steps, each with its own CFL
 time step, so its result does not depend on what else is in the batch.
 
 The GPU work runs in the C library (dg_batch_*); this module only schedules.
 """
+import collections
 import dataclasses
 import math
 import time
@@ -137,24 +139,71 @@ class Server:
         for q in pending:
             if q.device_bytes() > self.budget:
                 raise ValueError(f"request {q.rid} needs {q.device_bytes()} B, above the budget")
-        waiting, active = [], []      # active: [request, remaining steps, admit time]
+        waiting = []
+        # active: [request, steps not yet enqueued, steps not yet completed, admit time]
+        active = []
+        inflight = collections.deque()   # enqueued steps: (token, k)
         outcomes = []
         used = peak = peak_active = iters = rebuilds = 0
         dof_stage = rebuild_s = enqueue_s = wait_s = 0.0
         t0 = self.clock()
         changed = False
         i = 0
-        while i < len(pending) or waiting or active:
-            now = self.clock() - t0
+
+        def arrive(now):
+            nonlocal i
             while i < len(pending) and pending[i].arrival <= now:
                 waiting.append(pending[i])
                 i += 1
-            # first come, first served while the head of the queue fits
+
+        def enqueue():
+            nonlocal enqueue_s
+            k = 2 if all(a[1] >= 2 for a in active) else 1
+            tr = self.clock()
+            token = self.ex.step(k)
+            enqueue_s += self.clock() - tr
+            for a in active:
+                a[1] -= k
+            inflight.append((token, k))
+
+        while i < len(pending) or waiting or active:
+            now = self.clock() - t0
+            arrive(now)
+            if inflight:
+                # one more step before waiting, when it cannot change what
+                # is active: nobody's last step is in flight and nobody
+                # waiting could be admitted now
+                if (len(inflight) < 2 and all(a[1] > 0 for a in active)
+                        and not (waiting and used + waiting[0].device_bytes() <= self.budget)):
+                    enqueue()
+                token, k = inflight.popleft()
+                tw = self.clock()
+                if not self.ex.wait(self.deadline, token):
+                    raise TimeoutError_(f"step did not finish within {self.deadline} s")
+                wait_s += self.clock() - tw
+                iters += 1
+                done_t = self.clock() - t0
+                still = []
+                for a in active:
+                    q = a[0]
+                    a[2] -= k
+                    dof_stage += 5.0 * k * q.dof
+                    if a[2] == 0:
+                        res = self.ex.finish(q, keep_state=self.keep_states)
+                        used -= q.device_bytes()
+                        outcomes.append(Outcome(q.rid, q.arrival, a[3], done_t, q.nsteps, res))
+                        changed = True
+                    else:
+                        still.append(a)
+                active = still
+                continue
+            # nothing in flight: admissions (first come, first served while
+            # the head of the queue fits), the batch for the new active set
             while waiting and used + waiting[0].device_bytes() <= self.budget:
                 q = waiting.pop(0)
                 self.ex.admit(q)
                 used += q.device_bytes()
-                active.append([q, q.nsteps, now])
+                active.append([q, q.nsteps, q.nsteps, now])
                 changed = True
             peak = max(peak, used)
             peak_active = max(peak_active, len(active))
@@ -168,29 +217,7 @@ class Server:
                 rebuild_s += self.clock() - tr
                 rebuilds += 1
                 changed = False
-            k = 2 if all(a[1] >= 2 for a in active) else 1
-            tr = self.clock()
-            self.ex.step(k)
-            tw = self.clock()
-            enqueue_s += tw - tr
-            if not self.ex.wait(self.deadline):
-                raise TimeoutError_(f"step did not finish within {self.deadline} s")
-            wait_s += self.clock() - tw
-            iters += 1
-            done_t = self.clock() - t0
-            still = []
-            for a in active:
-                q = a[0]
-                a[1] -= k
-                dof_stage += 5.0 * k * q.dof
-                if a[1] == 0:
-                    res = self.ex.finish(q, keep_state=self.keep_states)
-                    used -= q.device_bytes()
-                    outcomes.append(Outcome(q.rid, q.arrival, a[2], done_t, q.nsteps, res))
-                    changed = True
-                else:
-                    still.append(a)
-            active = still
+            enqueue()
         wall = self.clock() - t0
         return Report(sorted(outcomes, key=lambda o: o.rid), wall, dof_stage, peak, peak_active,
                       iters, rebuilds, rebuild_s, enqueue_s, wait_s)
@@ -213,7 +240,6 @@ class GpuExecutor:
         self.handles = {}     # rid -> dict(Q, dQ, Qt, fresh, req)
         self.groups = []      # [(cfl, Batch, [rid, ...])]
         self.where = {}       # rid -> (group index, index in the batch)
-        self.event = None
 
     def admit(self, q):
         t = self.torch
@@ -257,16 +283,18 @@ class GpuExecutor:
                 self.groups.append((cfl, batch, [q.rid for q in members]))
 
     def step(self, k):
+        """Enqueue k steps of every group; returns the event that marks their end."""
         with self.torch.cuda.stream(self.stream):
             for cfl, batch, _ in self.groups:
                 batch.step(cfl, nsteps=k, use_graph=True)
-            self.event = self.torch.cuda.Event()
-            self.event.record(self.stream)
+            event = self.torch.cuda.Event()
+            event.record(self.stream)
+        return event
 
-    def wait(self, deadline_s):
-        """Poll the step's event until it completes or the deadline passes."""
+    def wait(self, deadline_s, event):
+        """Poll a step's event until it completes or the deadline passes."""
         t_end = time.perf_counter() + deadline_s
-        while not self.event.query():
+        while not event.query():
             if time.perf_counter() > t_end:
                 return False
             time.sleep(20e-6)
@@ -306,8 +334,9 @@ class FakeExecutor:
 
     def step(self, k):
         self.clock.advance(k * self.cost * sum(q.dof for q in self.active))
+        return k
 
-    def wait(self, deadline_s):
+    def wait(self, deadline_s, token):
         return True
 
     def finish(self, q, keep_state=False):

@@ -61,9 +61,57 @@ def test_oversize_request_rejected():
 
 def test_step_deadline():
     class Stuck(serve.FakeExecutor):
-        def wait(self, deadline_s):
+        def wait(self, deadline_s, token):
             return False
 
     clock = serve.ManualClock()
     with pytest.raises(serve.TimeoutError_):
         serve.Server(Stuck(clock), 10 ** 12, clock=clock, step_deadline_s=0.01).run(_reqs(2))
+
+
+class Tracking(serve.FakeExecutor):
+    """FakeExecutor that checks the pipelining rules: at most two steps in
+    flight, and batch changes (rebuild) and result reads (finish) only with
+    nothing in flight; records every request's steps."""
+
+    def __init__(self, clock, cost_per_dof_step=1e-9):
+        super().__init__(clock, cost_per_dof_step)
+        self.outstanding = 0
+        self.max_outstanding = 0
+        self.steps_of = {}
+
+    def step(self, k):
+        self.outstanding += 1
+        assert self.outstanding <= 2
+        self.max_outstanding = max(self.max_outstanding, self.outstanding)
+        for q in self.active:
+            self.steps_of[q.rid] = self.steps_of.get(q.rid, 0) + k
+        return super().step(k)
+
+    def wait(self, deadline_s, token):
+        self.outstanding -= 1
+        return True
+
+    def rebuild(self, reqs):
+        assert self.outstanding == 0
+        super().rebuild(reqs)
+
+    def finish(self, q, keep_state=False):
+        assert self.outstanding == 0
+        return super().finish(q, keep_state)
+
+
+def test_pipelined_steps_keep_exact_step_counts():
+    # requests arriving at once under a budget that holds a few: joins and
+    # leaves between steps, and a second step enqueued behind the one in
+    # flight whenever the active set cannot change
+    clock = serve.ManualClock()
+    ex = Tracking(clock, cost_per_dof_step=1e-8)
+    reqs = _reqs(10, rate=1e6)
+    budget = 3 * max(q.device_bytes() for q in reqs)
+    rep = serve.Server(ex, budget, clock=clock).run(reqs)
+    assert sorted(o.rid for o in rep.outcomes) == sorted(q.rid for q in reqs)
+    for q in reqs:
+        assert ex.steps_of[q.rid] == q.nsteps, q
+    assert ex.max_outstanding == 2
+    assert ex.outstanding == 0
