@@ -947,7 +947,19 @@ dg_status dg_batch_update(dg_batch *b, int n, const dg_instance *desc)
     dg_status st = check_instances(n, desc);
     if (st != DG_OK) return st;
     st = batch_assign(b, n, desc);
-    if (st != DG_OK) cudaGetLastError();
+    if (st != DG_OK) {
+        cudaGetLastError();  // clear a sticky allocation error
+        // a half-built list is never stepped: the batch holds no instances
+        b->n = 0;
+        b->inst.clear();
+        b->dofs.clear();
+        b->direct.clear();
+        b->items.clear();
+        b->litems.clear();
+        b->lane_of.clear();
+        b->nlanes = 0;
+        for (int N = 0; N <= dg::NMAX; ++N) b->lbeg[N] = b->lend[N] = 0;
+    }
     return st;
 }
 
@@ -991,6 +1003,7 @@ dg_status dg_batch_state_init(const dg_batch *b, int idx, dg_init_kind kind, con
 dg_status dg_batch_step(dg_batch *b, double cfl, int nsteps, int use_graph, void *stream)
 {
     if (!b || !finite_pos(cfl) || nsteps < 0) return DG_ERR_ARG;
+    if (b->n == 0) return DG_OK;  // no instances (after a failed dg_batch_update)
     cudaStream_t s = as_stream(stream);
     if (!use_graph) {
         cudaError_t e = cudaSuccess;

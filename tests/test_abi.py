@@ -125,3 +125,23 @@ def test_committed_tuning_table_applies():
         for p, (v, k) in saved.items():
             dg.dg_set_tile_variant(p, v)
             dg.dg_set_stage_kernel(p, k)
+
+
+def test_new_entry_points_reject_bad_arguments_on_host(lib):
+    """The z-slab, batch-update, probe and self-check entry points validate
+    their arguments before any CUDA call (no GPU needed)."""
+    vp, i = ctypes.c_void_p, ctypes.c_int
+    lib.dg_rk_stage.argtypes = [vp, vp, vp, vp, vp, i, vp]
+    assert lib.dg_rk_stage(None, None, None, None, None, 0, None) == 1
+    lib.dg_mesh_set_zhalo.argtypes = [vp, vp, vp]
+    assert lib.dg_mesh_set_zhalo(None, None, None) == 1
+    lib.dg_zhalo_traces.argtypes = [vp, vp, vp, vp, vp]
+    assert lib.dg_zhalo_traces(None, None, None, None, None) == 1
+    lib.dg_batch_update.argtypes = [vp, i, vp]
+    assert lib.dg_batch_update(None, 1, None) == 1
+    lib.dg_fma_throughput.argtypes = [i, vp, vp]
+    assert lib.dg_fma_throughput(0, None, None) == 1
+    lib.dg_dmma_throughput.argtypes = [i, vp, vp]
+    assert lib.dg_dmma_throughput(2, None, None) == 1
+    lib.dg_selfcheck_sqrt.argtypes = [vp, vp, vp, ctypes.c_int64, vp]
+    assert lib.dg_selfcheck_sqrt(None, None, None, 4, None) == 1
