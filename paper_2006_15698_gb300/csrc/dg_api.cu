@@ -675,7 +675,7 @@ cudaError_t batch_enqueue(const dg_batch *b, double cfl, int nsteps, cudaStream_
         // stream when the batch has a single unit of work)
         for (int N = 1; N <= dg::NMAX && e == cudaSuccess; ++N) {
             if (b->lend[N] <= b->lbeg[N]) continue;
-            cudaStream_t ls = b->nlanes > 0 ? b->lane[b->group_lane[N]] : s;
+            cudaStream_t ls = (b->nlanes > 0 && b->group_lane[N] >= 0) ? b->lane[b->group_lane[N]] : s;
             for (int st = 0; st < 5 && e == cudaSuccess; ++st)
                 e = dg::batch_line_stage(b->d_litems + b->lbeg[N], b->lend[N] - b->lbeg[N],
                                          b->d_inst, N, parity ^ (st & 1), (float)kA[st],
@@ -873,16 +873,18 @@ dg_status batch_assign(dg_batch *b, int n, const dg_instance *desc)
     // grid of the time-step reduction: as many CTAs as fit
     const int ni = (int)b->items.size();
     b->grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * 8, (long long)ni));
-    // lanes: the units of stage work -- each large instance, and the shared
-    // instances of each order N (one launch per stage) -- largest first onto
-    // the least loaded lane
+    // lanes: the units of stage work -- each large instance; and, when there
+    // is no large instance, the shared instances of each order N (one launch
+    // per stage) -- largest first onto the least loaded lane.  Next to large
+    // instances the orders' launches stay on the caller's stream, where they
+    // overlap the lanes.
     std::vector<long long> unit_dof;  // direct instances first, then the orders
     std::vector<int> unit_N;
     for (int k : b->direct) {
         unit_dof.push_back(b->dofs[k]);
         unit_N.push_back(0);
     }
-    for (int N = 1; N <= dg::NMAX; ++N) {
+    for (int N = 1; N <= dg::NMAX && b->direct.empty(); ++N) {
         if (b->lend[N] <= b->lbeg[N]) continue;
         long long d = 0;
         for (int i = 0; i < n; ++i)
@@ -890,6 +892,7 @@ dg_status batch_assign(dg_batch *b, int n, const dg_instance *desc)
         unit_dof.push_back(d);
         unit_N.push_back(N);
     }
+    for (int N = 0; N <= dg::NMAX; ++N) b->group_lane[N] = -1;
     b->lane_of.assign(b->direct.size(), 0);
     if (unit_dof.size() > 1) {
         b->nlanes = (int)std::min<size_t>(dg_batch::kLanes, unit_dof.size());
