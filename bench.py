@@ -80,8 +80,8 @@ WORKLOADS["batch256_fp32"] = dict(
     kind="batch", count=256, nrange=(4, 32), prange=(1, 5), seed=0, prec="fp32", cfl=0.5,
     box=(0, 0, 0, 10.0, 10.0, 10.0), p=3, nel=(1, 1, 1), init="vortex", params=None,
     desc="256 independent isentropic-vortex instances, elements per side uniform in 4..32 and p "
-         "uniform in 1..5 (seed 0), FP32, one persistent launch per RK stage, CUDA-graph step, "
-         "tile shape per p from the autotuner table")
+         "uniform in 1..5 (seed 0), FP32, shared line-kernel launches per RK stage and degree for "
+         "the small instances and own launches on four streams for the others, CUDA-graph step")
 WORKLOADS["batch64_fp32"] = dict(WORKLOADS["batch256_fp32"], count=64,
                                  desc="64 instances of the batch256_fp32 distribution (profiling)")
 WORKLOADS["serve2000_fp32"] = dict(
@@ -162,7 +162,7 @@ def batch_specs(w):
 
 def run_batch(args, w):
     """The batched form: every instance of the batch advanced one LSERK45 step
-    per bench step (graph replay of CFL + 5 persistent stage launches + copy)."""
+    per bench step (graph replay: time steps, five stages, copy back)."""
     import torch
     from paper_2006_15698_gb300 import dg, inputs
     ws, rank, local = _dist()
@@ -374,10 +374,17 @@ def _dist():
 
 
 def _kernel_hash():
+    """Hash of the kernel sources' code (comments and whitespace removed: the
+    compiled kernels do not depend on them), to tell whether committed ncu
+    counters were taken on the current kernels."""
+    import re
     h = hashlib.sha256()
     for f in ("dg_kernels.cuh", "dg_fused.cuh", "dg_column.cuh", "dg_lines.cuh"):
-        with open(os.path.join(ROOT, "paper_2006_15698_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2006_15698_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

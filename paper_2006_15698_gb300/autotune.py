@@ -5,8 +5,9 @@ float mesh (isentropic vortex, about `target_dof` nodes) with each tile
 variant the library offers (dg_tile_variant_count / dg_tile_shape) and with
 the two column kernels (one thread per node, "column"; one thread per z node
 line, "lines"), and writes the table that ``dg.load_tuning`` reads: the
-fastest tile variant (used by batches, and by single meshes when "kernel" is
-"tile") and the fastest single-mesh kernel:
+fastest tile variant (used by single meshes when "kernel" is "tile") and the
+fastest single-mesh kernel (which a batch's own-launch instances use; its
+shared instances always run the line kernel):
 
     {"gpu": ..., "degrees": {"3": {"variant": 1, "tile": [2, 2], "kernel": "lines",
                                    "ms_per_step": {"0": 5.1, "1": 4.8, "column": 4.1,

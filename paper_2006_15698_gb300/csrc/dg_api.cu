@@ -583,7 +583,7 @@ struct dg_batch {
     bool small = true;              // every instance's offsets fit a 32-bit int
     std::vector<int> direct;        // large instances: launched by themselves
     // streams the large instances' stage launches run on, concurrently with
-    // each other and with the persistent launches (forked from and joined to
+    // each other and with the shared launches (forked from and joined to
     // the caller's stream every step); lane_of[k]: the lane of direct[k]
     static constexpr int kLanes = 4;
     int nlanes = 0;
@@ -624,7 +624,7 @@ void batch_free(dg_batch *b)
 
 // Instances of at least this many nodes run their own launches of the
 // single-mesh stage kernels (inside the batch's step and graph, on the
-// batch's lanes); the smaller ones share the persistent batched launches.
+// batch's lanes); the smaller ones share the batched line-kernel launches.
 // Process-wide, read by dg_batch_create (dg_set_batch_direct_nodes).
 std::atomic<long long> g_direct_nodes{1LL << 13};
 

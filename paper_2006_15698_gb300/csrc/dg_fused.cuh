@@ -1,6 +1,7 @@
-// dg_fused.cuh -- the float form's fused single-pass RK stage (faces + volume
-// + lift + update in one kernel), for one mesh and for a batch of independent
-// meshes in one persistent launch.  Included by dg_kernels.cuh.
+// dg_fused.cuh -- the float form's fused single-pass RK stage on element
+// tiles (faces + volume + lift + update in one kernel) for one mesh, and the
+// time-step reduction of a batch of independent meshes.  Included by
+// dg_kernels.cuh.
 //
 // For the float form the stage is bound by DRAM traffic and instruction
 // issue, not by a narrow pipe, so one kernel does all of it: a CTA stages a
