@@ -379,7 +379,8 @@ def _kernel_hash():
     counters were taken on the current kernels."""
     import re
     h = hashlib.sha256()
-    for f in ("dg_kernels.cuh", "dg_fused.cuh", "dg_column.cuh", "dg_lines.cuh"):
+    for f in ("dg_kernels.cuh", "dg_fused.cuh", "dg_column.cuh", "dg_lines.cuh",
+              "dg_line_body.inc"):
         with open(os.path.join(ROOT, "paper_2006_15698_gb300", "csrc", f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)

@@ -1044,11 +1044,16 @@ cudaError_t launch_column_ix(const Geo &g, const Ops<float> &T, const float *Qin
     using LT = LineTile<N, TX, TY, LineShape<N, 0>::NS, LineShape<N, 0>::RPAD>;
     constexpr int THREADS = LINES ? LT::THREADS : ColTile<N, TX, TY>::THREADS;
     constexpr size_t BYTES = LINES ? LT::BYTES : ColTile<N, TX, TY>::BYTES;
-    auto kernel = LINES ? line_stage_kernel<N, 0, MODE, Ix> : column_stage_kernel<N, 0, MODE, Ix>;
-    // CTAs of this kernel resident on a device at once, per device (a benign
-    // race: concurrent first calls store the same value)
+    // a z slab's line kernel (halo reads compiled in) or the periodic one;
+    // the column kernel tests for halos at run time
+    const bool halo = LINES && g.zlo != nullptr;
+    auto kernel = !LINES ? column_stage_kernel<N, 0, MODE, Ix>
+                  : halo ? line_stage_kernel<N, 0, MODE, Ix, true>
+                         : line_stage_kernel<N, 0, MODE, Ix, false>;
+    // CTAs of this kernel resident on a device at once, per device and
+    // variant (a benign race: concurrent first calls store the same value)
     constexpr int kDevices = 64;
-    static int resident_of[kDevices] = {};
+    static int resident_of[2][kDevices] = {};
     if (BYTES > 48 * 1024) {
         cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)BYTES);
@@ -1057,7 +1062,7 @@ cudaError_t launch_column_ix(const Geo &g, const Ops<float> &T, const float *Qin
     int dev = 0;
     cudaError_t derr = cudaGetDevice(&dev);
     if (derr != cudaSuccess) return derr;
-    int resident = dev < kDevices ? resident_of[dev] : 0;
+    int resident = dev < kDevices ? resident_of[halo][dev] : 0;
     if (resident == 0) {
         int sms = 0, per_sm = 0;
         cudaError_t err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1065,7 +1070,7 @@ cudaError_t launch_column_ix(const Geo &g, const Ops<float> &T, const float *Qin
             err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, THREADS, BYTES);
         if (err != cudaSuccess) return err;
         resident = sms * (per_sm > 0 ? per_sm : 1);
-        if (dev < kDevices) resident_of[dev] = resident;
+        if (dev < kDevices) resident_of[halo][dev] = resident;
     }
     const long long ncols = (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
     int best_zc = g.nz;
