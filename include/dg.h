@@ -219,11 +219,15 @@ dg_status dg_norms(const dg_mesh *mesh, const void *Q, const void *Qref, double 
  *     dts[k]                     = the dg_cfl_dt time step of the current Q,
  *     Q                          <- dg_rk_step(Q, dQ, &dts[k]),
  *     integ[k*DG_NORMS_LEN ...]  = dg_norms(Q, NULL) of the new Q (if integ).
- * The results are those of the separate calls, bit for bit.  The integrals
- * of a step and the maximum wave speed for the next step's time step come
- * from one pass over the new state; for DG_FP32 that pass also applies the
- * fifth stage's update Q <- Q + B_5 dQ in place (the fifth stage writes only
- * dQ), so the copy of the ping-pong state that dg_rk_step makes is not needed.
+ * Q, dts and integ are those of the separate calls, bit for bit.  The
+ * integrals of a step and the maximum wave speed for the next step's time
+ * step come from one read of the new state.  DG_FP32: the steps alternate
+ * between Q and the handle's second state (a step's fifth stage writes only
+ * the new state, into the buffer the step did not start from; the next
+ * step's first stage does not read dQ), so no copy of the state is made per
+ * step; after an odd nsteps the result is copied into Q once.  On return dQ
+ * holds the RK register of the last step's fourth stage (DG_FP32; DG_FP64:
+ * as dg_rk_step leaves it): callers treat it as scratch.
  * dts and integ (nullable) are DEVICE arrays of nsteps and
  * nsteps * DG_NORMS_LEN doubles; Q and dQ as for dg_rk_step.  A non-positive
  * density or pressure met by any time-step evaluation sets the

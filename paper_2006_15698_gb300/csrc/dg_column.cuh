@@ -312,8 +312,9 @@ __device__ __forceinline__ void plane_interface(const float *__restrict__ Qin, c
 }
 
 // One column chunk of the stage.  MODE 0 writes the rhs to Out, MODE 1 the
-// LSERK stage update (dQ <- A dQ + dt R, Out <- Qin + B dQ), MODE 2 only its
-// dQ part (a step's last stage when a later pass applies Out <- Qin + B dQ).  Ix is the index
+// LSERK stage update (dQ <- A dQ + dt R, Out <- Qin + B dQ), MODE 2 a step's
+// last stage, whose dQ no later stage reads: only Out <- Qin + B (A dQ + dt R),
+// dQ left as it was.  Ix is the index
 // type of the state arrays: int when 5 E N^3 fits (32-bit address arithmetic
 // is measurably cheaper here), else a 64-bit integer.
 // (shared memory holds about four CTAs per SM; registers are sized for that)
@@ -512,7 +513,7 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
                 load_line<N>(f + 1 * NF * N3 + n * N3 + (k * N + i) * N, vy);
                 load_line<N>(f + 2 * NF * N3 + n * N3 + (j * N + i) * N, vz);
                 // packed pairs, explicitly rounded: every instantiation (rhs,
-                // stage, dQ-only last stage) gives the same floats
+                // stage, a step's last stage) gives the same floats
                 float2 a2 = f2(0.0f, 0.0f);
                 a2 = dot2_acc<N>(dx, vx, a2);
                 a2 = dot2_acc<N>(dy, vy, a2);
@@ -528,8 +529,8 @@ __global__ void __launch_bounds__(ColTile<N, ColShape<N, V>::TX, ColShape<N, V>:
                     Out[o] = acc;
                 } else {
                     const float d = __fmaf_rn(dtr, acc, A == 0.0f ? 0.0f : __fmul_rn(A, dq[n]));
-                    dQ[o] = d;
-                    if (MODE == 1) Out[o] = __fmaf_rn(B, d, cur[(n * EPB + el) * CT::ESTR + node]);
+                    if (MODE == 1) dQ[o] = d;
+                    Out[o] = __fmaf_rn(B, d, cur[(n * EPB + el) * CT::ESTR + node]);
                 }
             }
         }

@@ -208,7 +208,8 @@ __device__ __forceinline__ void fused_face(const float *__restrict__ Qin, const 
 // One tile of the stage with blockDim.x >= TX*TY*N^3 threads (one per node;
 // extra threads only help with the face tasks).  MODE 0 writes the rhs to
 // Out, MODE 1 the LSERK stage update (dQ <- A dQ + dt R, Out <- Qin + B dQ),
-// MODE 2 only its dQ part (a later pass applies Out <- Qin + B dQ).
+// MODE 2 a step's last stage, whose dQ no later stage reads: only
+// Out <- Qin + B (A dQ + dt R), dQ left as it was.
 // Ends with a barrier, so a persistent caller may reuse `smem` at once.
 // Ix: index type of the state arrays (32-bit when every offset fits).
 template <int N, int TX, int TY, int MODE, typename Ix = long long>
@@ -347,7 +348,7 @@ __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float 
             const float2 hx = *reinterpret_cast<const float2 *>(h + ((0 * NF + n) * N2 + px) * 2);
             const float2 hy = *reinterpret_cast<const float2 *>(h + ((1 * NF + n) * N2 + py) * 2);
             const float2 hz = *reinterpret_cast<const float2 *>(h + ((2 * NF + n) * N2 + pz) * 2);
-            // explicitly rounded: every instantiation (rhs, stage, dQ-only
+            // explicitly rounded: every instantiation (rhs, stage, a step's
             // last stage) gives the same floats
             acc = __fmaf_rn(-lpx, hx.y, __fmaf_rn(lmx, hx.x, acc));
             acc = __fmaf_rn(-lpy, hy.y, __fmaf_rn(lmy, hy.x, acc));
@@ -358,8 +359,8 @@ __device__ __forceinline__ void fused_tile(const float *__restrict__ Qin, float 
                 Out[o] = acc;
             } else {
                 const float d = __fmaf_rn(dtr, acc, A == 0.0f ? 0.0f : __fmul_rn(A, dQ[o]));
-                dQ[o] = d;
-                if (MODE == 1) Out[o] = __fmaf_rn(B, d, q[n]);
+                if (MODE == 1) dQ[o] = d;
+                Out[o] = __fmaf_rn(B, d, q[n]);
             }
         }
     }

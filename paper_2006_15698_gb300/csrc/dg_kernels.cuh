@@ -24,6 +24,7 @@
 #pragma once
 
 #include <type_traits>
+#include <utility>
 
 #include <cuda_runtime.h>
 
@@ -732,16 +733,15 @@ __global__ void __launch_bounds__(256) norms_partial_kernel(const real *__restri
     norms_block_store<real>(sh, acc, fh, fl, partials);
 }
 
-// Step epilogue of dg_advance, one pass over the state a step ends with:
-// UPDATE applies the float form's fifth-stage update Q <- Q + B dQ in place
-// (the fifth stage wrote only dQ); then the integrals of the new state (the
-// partition, order and arithmetic of norms_partial_kernel without Qref, so
-// the sums are those of dg_norms bit for bit) and, if CFL, its Lambda
-// maximum for the next step's time step (the node speeds of cfl_kernel).
-template <typename real, bool UPDATE, bool CFL, bool NORMS>
-__global__ void __launch_bounds__(256) step_epilogue_kernel(real *Q, const real *__restrict__ dQ,
-                                                            real B, const Geo g,
-                                                            const NodeWeights W, double *partials,
+// Step epilogue of dg_advance, one read of the state a step ends with: the
+// integrals of the new state if NORMS (the partition, order and arithmetic
+// of norms_partial_kernel without Qref, so the sums are those of dg_norms bit
+// for bit) and, if CFL, its Lambda maximum for the next step's time step (the
+// node speeds of cfl_kernel).
+template <typename real, bool CFL, bool NORMS>
+__global__ void __launch_bounds__(256) step_epilogue_kernel(const real *__restrict__ Q,
+                                                            const Geo g, const NodeWeights W,
+                                                            double *partials,
                                                             unsigned long long *lam_bits, int *err)
 {
     constexpr int U = kSweepU<real>;
@@ -782,26 +782,9 @@ __global__ void __launch_bounds__(256) step_epilogue_kernel(real *Q, const real 
             if (node >= N3) node -= N3;
 #pragma unroll
             for (int n = 0; n < NF; ++n) qr[u][n] = Q[n * nodes + t];
-            if constexpr (UPDATE) {
-                real d[NF];
-#pragma unroll
-                for (int n = 0; n < NF; ++n) d[n] = dQ[n * nodes + t];
-#pragma unroll
-                for (int n = 0; n < NF; ++n) {
-                    if constexpr (sizeof(real) == 4) qr[u][n] = __fmaf_rn(B, d[n], qr[u][n]);
-                    else qr[u][n] = __fma_rn(B, d[n], qr[u][n]);
-                }
-            }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const long long t = tb + (long long)u * bd + lane;
-            if constexpr (UPDATE) {
-                if (in[u]) {
-#pragma unroll
-                    for (int n = 0; n < NF; ++n) Q[n * nodes + t] = qr[u][n];
-                }
-            }
             if constexpr (NORMS) {
                 if (in[u]) norms_node<real>(sh, nd[u], qr[u], acc, fh, fl);
             }
@@ -1125,30 +1108,42 @@ cudaError_t rhs_n(const Geo &g, const Ops<real> &T, const real *Q, real *R, Work
     }
 }
 
+// The five float-form stages of one LSERK45 step, ping-ponging between two
+// states: cur -> other -> cur -> other -> cur -> other, the step's result in
+// other.  LAST_MODE 1: the fifth stage also leaves its dQ (dg_rk_step);
+// 2: it writes only the new state (dg_advance: the next step's first stage,
+// A_1 = 0, does not read dQ).
+template <int N, int LAST_MODE>
+cudaError_t float_step(const Geo &g, const Ops<float> &T, float *cur, float *other, float *dQ,
+                       const double *dt, Work &w, cudaStream_t s)
+{
+    for (int st = 0; st < 5; ++st) {
+        const float *src = (st % 2 == 0) ? cur : other;
+        float *dst = (st % 2 == 0) ? other : cur;
+        const float A = float(kRkA[st]), B = float(kRkB[st]);
+        cudaError_t err;
+        if (st == 4)
+            err = column_stage(N) ? launch_column<N, LAST_MODE>(g, T, src, dst, dQ, A, B, dt, w.prof, s)
+                                  : launch_fused<N, LAST_MODE>(g, T, src, dst, dQ, A, B, dt, w.prof, s);
+        else
+            err = column_stage(N) ? launch_column<N, 1>(g, T, src, dst, dQ, A, B, dt, w.prof, s)
+                                  : launch_fused<N, 1>(g, T, src, dst, dQ, A, B, dt, w.prof, s);
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
 // One LSERK45 step.  Float form: ping-pong between Q and the handle's second
-// state; the fifth stage ends in the second state, copied back so the result
-// is in Q -- unless last_dq_only, where the fifth stage writes only dQ, Q
-// holds the fourth stage's state, and the caller applies Q <- Q + B_5 dQ.
+// state; the fifth stage ends in the second state, copied back so that the
+// result is in Q.
 template <int N, typename real>
 cudaError_t rk_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, const double *dt, Work &w,
-                 cudaStream_t s, bool last_dq_only = false)
+                 cudaStream_t s)
 {
     if constexpr (std::is_same<real, float>::value) {
         real *Tq = static_cast<real *>(w.qtmp);
-        for (int st = 0; st < 5; ++st) {
-            const real *src = (st % 2 == 0) ? Q : Tq;
-            real *dst = (st % 2 == 0) ? Tq : Q;
-            const float A = float(kRkA[st]), B = float(kRkB[st]);
-            cudaError_t err;
-            if (st == 4 && last_dq_only)
-                err = column_stage(N) ? launch_column<N, 2>(g, T, src, dst, dQ, A, B, dt, w.prof, s)
-                                      : launch_fused<N, 2>(g, T, src, dst, dQ, A, B, dt, w.prof, s);
-            else
-                err = column_stage(N) ? launch_column<N, 1>(g, T, src, dst, dQ, A, B, dt, w.prof, s)
-                                      : launch_fused<N, 1>(g, T, src, dst, dQ, A, B, dt, w.prof, s);
-            if (err != cudaSuccess) return err;
-        }
-        if (last_dq_only) return cudaSuccess;
+        cudaError_t err = float_step<N, 1>(g, T, Q, Tq, dQ, dt, w, s);
+        if (err != cudaSuccess) return err;
         const size_t bytes = (size_t)NF * (size_t)g.E * N * N * N * sizeof(real);
         ProfScope ps(w.prof, kKindCopy, s);
         return cudaMemcpyAsync(Q, Tq, bytes, cudaMemcpyDeviceToDevice, s);
@@ -1270,12 +1265,11 @@ inline NodeWeights node_weights(const Geo &g)
     return W;
 }
 
-template <typename real, bool UPDATE, bool CFL, bool NORMS>
-void launch_epilogue(real *Q, const real *dQ, real B, const Geo &g, const NodeWeights &W, Work &w,
-                     cudaStream_t s)
+template <typename real, bool CFL, bool NORMS>
+void launch_epilogue(const real *Q, const Geo &g, const NodeWeights &W, Work &w, cudaStream_t s)
 {
-    step_epilogue_kernel<real, UPDATE, CFL, NORMS><<<kNormBlocks, 256, 0, s>>>(
-        Q, dQ, B, g, W, w.partials, w.lam_bits, w.err);
+    step_epilogue_kernel<real, CFL, NORMS><<<kNormBlocks, 256, 0, s>>>(Q, g, W, w.partials,
+                                                                       w.lam_bits, w.err);
 }
 
 // nsteps steps of (time step, LSERK45 step, integrals); the end of a step and
@@ -1359,49 +1353,67 @@ template <int N, typename real>
 cudaError_t advance_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, double cfl, int nsteps,
                       double *dts, double *integ, Work &w, cudaStream_t s)
 {
-    constexpr bool kFloat = std::is_same<real, float>::value;
-    const NodeWeights W = node_weights(g);
     cudaError_t err = Launch<real>::cfl(g, Q, cfl, dts, w, s);
     if (err != cudaSuccess) return err;
-    const real B5 = real(kRkB[4]);
-    for (int k = 0; k < nsteps; ++k) {
-        err = rk_n<N, real>(g, T, Q, dQ, dts + k, w, s, kFloat);
-        if (err != cudaSuccess) return err;
-        const bool more = k + 1 < nsteps, norms = integ != nullptr;
-        if constexpr (!kFloat) {
-            // double state: the integrals are FP64-pipe bound and the time
-            // step's pre-filter is warp-synchronous; one pass doing both was
-            // measured slower than the two passes, which it would only save
-            // one read of the state
+    const bool norms = integ != nullptr;
+    if constexpr (!std::is_same<real, float>::value) {
+        // double state: the integrals are FP64-pipe bound and the time step's
+        // pre-filter is warp-synchronous; one pass doing both was measured
+        // slower than the two passes, which it would only save one read of
+        // the state
+        for (int k = 0; k < nsteps; ++k) {
+            err = rk_n<N, real>(g, T, Q, dQ, dts + k, w, s);
+            if (err != cudaSuccess) return err;
             if (norms) {
                 err = Launch<real>::norms(g, Q, nullptr, integ + (size_t)k * DG_NORMS_LEN, w, s);
                 if (err != cudaSuccess) return err;
             }
-            if (more) {
+            if (k + 1 < nsteps) {
                 err = Launch<real>::cfl(g, Q, cfl, dts + k + 1, w, s);
                 if (err != cudaSuccess) return err;
             }
-            continue;
         }
-        ProfScope ps(w.prof, kKindEpilogue, s);
-        if (more && norms) launch_epilogue<real, kFloat, true, true>(Q, dQ, B5, g, W, w, s);
-        else if (more) launch_epilogue<real, kFloat, true, false>(Q, dQ, B5, g, W, w, s);
-        else if (norms) launch_epilogue<real, kFloat, false, true>(Q, dQ, B5, g, W, w, s);
-        else if (kFloat) launch_epilogue<real, kFloat, false, false>(Q, dQ, B5, g, W, w, s);
-        err = cudaGetLastError();
-        if (err != cudaSuccess) return err;
-        if (norms) {
-            norms_final_kernel<<<1, 256, 0, s>>>(w.partials, kNormBlocks, 0, integ + (size_t)k * DG_NORMS_LEN);
+        return cudaSuccess;
+    } else {
+        // float state: the steps alternate between Q and the second state
+        // (each step's fifth stage writes only the new state, into the buffer
+        // the step did not start from), and one read of each step's result
+        // gives its integrals and the next time step; an odd number of steps
+        // ends with a copy back into Q
+        const NodeWeights W = node_weights(g);
+        float *cur = Q, *other = static_cast<float *>(w.qtmp);
+        for (int k = 0; k < nsteps; ++k) {
+            err = float_step<N, 2>(g, T, cur, other, dQ, dts + k, w, s);
+            if (err != cudaSuccess) return err;
+            std::swap(cur, other);
+            const bool more = k + 1 < nsteps;
+            if (!more && !norms) break;
+            {
+                ProfScope ps(w.prof, kKindEpilogue, s);
+                if (more && norms) launch_epilogue<float, true, true>(cur, g, W, w, s);
+                else if (more) launch_epilogue<float, true, false>(cur, g, W, w, s);
+                else launch_epilogue<float, false, true>(cur, g, W, w, s);
+            }
             err = cudaGetLastError();
             if (err != cudaSuccess) return err;
+            if (norms) {
+                norms_final_kernel<<<1, 256, 0, s>>>(w.partials, kNormBlocks, 0, integ + (size_t)k * DG_NORMS_LEN);
+                err = cudaGetLastError();
+                if (err != cudaSuccess) return err;
+            }
+            if (more) {
+                cfl_finalize_kernel<<<1, 1, 0, s>>>(w.lam_bits, cfl, g.hmin, g.p, dts + k + 1);
+                err = cudaGetLastError();
+                if (err != cudaSuccess) return err;
+            }
         }
-        if (more) {
-            cfl_finalize_kernel<<<1, 1, 0, s>>>(w.lam_bits, cfl, g.hmin, g.p, dts + k + 1);
-            err = cudaGetLastError();
-            if (err != cudaSuccess) return err;
+        if (cur != Q) {
+            const size_t bytes = (size_t)NF * (size_t)g.E * N * N * N * sizeof(float);
+            ProfScope ps(w.prof, kKindCopy, s);
+            return cudaMemcpyAsync(Q, cur, bytes, cudaMemcpyDeviceToDevice, s);
         }
+        return cudaSuccess;
     }
-    return cudaSuccess;
 }
 
 // Explicit instantiation of the per-degree launch paths of one scalar type:
@@ -1412,7 +1424,7 @@ cudaError_t advance_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, doubl
     KW cudaError_t rhs_n<NN, REAL>(const Geo &, const Ops<REAL> &, const REAL *, REAL *, Work &, \
                                    cudaStream_t);                                            \
     KW cudaError_t rk_n<NN, REAL>(const Geo &, const Ops<REAL> &, REAL *, REAL *,             \
-                                  const double *, Work &, cudaStream_t, bool);               \
+                                  const double *, Work &, cudaStream_t);                     \
     KW cudaError_t advance_n<NN, REAL>(const Geo &, const Ops<REAL> &, REAL *, REAL *, double, \
                                        int, double *, double *, Work &, cudaStream_t);       \
     KW cudaError_t stage_n<NN, REAL>(const Geo &, const Ops<REAL> &, const REAL *, REAL *,     \
