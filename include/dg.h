@@ -236,6 +236,22 @@ dg_status dg_norms(const dg_mesh *mesh, const void *Q, const void *Qref, double 
 dg_status dg_advance(const dg_mesh *mesh, void *Q, void *dQ, double cfl, int nsteps,
                      double *dts, double *integ, void *stream);
 
+/* dg_advance on a state that lives in HOST memory (an addition of this
+ * library): Q_host (the state, layout as above, read and overwritten) is
+ * copied into the device state Q, dg_advance runs nsteps steps on the device
+ * (Q, dQ: caller-owned device buffers as for dg_advance), and the new state,
+ * the nsteps time steps and (if integ_host is not NULL) the nsteps *
+ * DG_NORMS_LEN integrals are copied back into Q_host, dts_host and
+ * integ_host.  The call returns once `stream` has finished all of it
+ * (synchronises).  Host buffers should be page-locked (cudaHostAlloc, a
+ * pinned torch tensor): pageable memory works but is staged by the driver.
+ * The time steps and integrals pass through a device buffer the mesh keeps
+ * for the largest nsteps so far (the first call, or a larger nsteps,
+ * allocates it: not for code that cannot allocate).  Errors: those of
+ * dg_advance (checked before any copy), DG_ERR_OOM, DG_ERR_CUDA. */
+dg_status dg_advance_host(dg_mesh *mesh, void *Q_host, void *Q, void *dQ, double cfl, int nsteps,
+                          double *dts_host, double *integ_host, void *stream);
+
 /* Per-kernel timing, the library's counterpart of the per-kernel breakdown
  * the paper reports (Sec. VI.B, Table II: Volume, Surface, Update-Project).
  * Between dg_profile_begin and dg_profile_end every kernel launch made for

@@ -3,6 +3,7 @@
 // handle's device workspace, and dispatch to the per-precision launchers.
 #include <atomic>
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -21,6 +22,10 @@ struct dg_mesh {
     dg::Prof *prof;
     int device;
     size_t ws_bytes;
+    // dg_advance_host: device time steps and integrals of the largest call
+    // so far (allocated on first use)
+    double *io = nullptr;
+    size_t io_cap = 0;
 };
 
 namespace {
@@ -243,6 +248,7 @@ void dg_mesh_destroy(dg_mesh *m)
     cudaFree(m->work.partials);
     cudaFree(m->work.lam_bits);
     cudaFree(m->work.err);
+    cudaFree(m->io);
     if (m->prof) {
         for (cudaEvent_t e : m->prof->ev) cudaEventDestroy(e);
         for (cudaEvent_t e : m->prof->pool) cudaEventDestroy(e);
@@ -333,6 +339,46 @@ dg_status dg_advance(const dg_mesh *m, void *Q, void *dQ, double cfl, int nsteps
                                                       cfl, nsteps, dts, integ, w, as_stream(stream))
                         : dg::Launch<float>::advance(m->geo, m->ops32, (float *)Q, (float *)dQ,
                                                      cfl, nsteps, dts, integ, w, as_stream(stream));
+    return cuda_status(e);
+}
+
+dg_status dg_advance_host(dg_mesh *m, void *Q_host, void *Q, void *dQ, double cfl, int nsteps,
+                          double *dts_host, double *integ_host, void *stream)
+{
+    if (!m || !Q_host || !dts_host || !Q || !dQ || Q == dQ || !aligned16(Q) || !aligned16(dQ) ||
+        nsteps < 1 || !(cfl > 0.0) || !std::isfinite(cfl))
+        return DG_ERR_ARG;
+    if (m->geo.zlo) return DG_ERR_UNSUPPORTED;
+    const int N = m->geo.p + 1;
+    const size_t per = (size_t)(1 + (integ_host ? DG_NORMS_LEN : 0));
+    if ((size_t)nsteps > (SIZE_MAX / sizeof(double)) / per) return DG_ERR_ARG;
+    const size_t need = (size_t)nsteps * per;
+    if (need > m->io_cap) {
+        cudaFree(m->io);
+        m->io = nullptr;
+        m->io_cap = 0;
+        cudaError_t e = cudaMalloc((void **)&m->io, need * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();  // not sticky: the context stays usable
+            return DG_ERR_OOM;
+        }
+        m->io_cap = need;
+    }
+    cudaStream_t s = as_stream(stream);
+    const size_t bytes = (size_t)dg::NF * (size_t)m->geo.E * N * N * N *
+                         (m->prec == DG_FP64 ? sizeof(double) : sizeof(float));
+    double *dts = m->io, *integ = integ_host ? m->io + nsteps : nullptr;
+    cudaError_t e = cudaMemcpyAsync(Q, Q_host, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    const dg_status st = dg_advance(m, Q, dQ, cfl, nsteps, dts, integ, stream);
+    if (st != DG_OK) return st;
+    e = cudaMemcpyAsync(Q_host, Q, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dts_host, dts, (size_t)nsteps * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && integ_host)
+        e = cudaMemcpyAsync(integ_host, integ, (size_t)nsteps * DG_NORMS_LEN * sizeof(double),
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return cuda_status(e);
 }
 

@@ -55,6 +55,8 @@ _lib.dg_norms.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.dg_norms.restype = ctypes.c_int
 _lib.dg_advance.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _vp, _vp, _vp]
 _lib.dg_advance.restype = ctypes.c_int
+_lib.dg_advance_host.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _vp, _vp, _vp]
+_lib.dg_advance_host.restype = ctypes.c_int
 _lib.dg_rk_stage.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.dg_rk_stage.restype = ctypes.c_int
 _lib.dg_mesh_set_zhalo.argtypes = [_vp, _vp, _vp]
@@ -238,6 +240,11 @@ def dg_advance(h, Q, dQ, cfl, nsteps, dts_dev, integ_dev, stream=None):
                            _stream(stream)), "dg_advance")
 
 
+def dg_advance_host(h, Q_host, Q, dQ, cfl, nsteps, dts_host, integ_host, stream=None):
+    _check(_lib.dg_advance_host(h, _ptr(Q_host), _ptr(Q), _ptr(dQ), cfl, nsteps, _ptr(dts_host),
+                                _ptr(integ_host), _stream(stream)), "dg_advance_host")
+
+
 def dg_rk_stage(h, Qin, Qout, dQ, dt_dev, stage, stream=None):
     _check(_lib.dg_rk_stage(h, _ptr(Qin), _ptr(Qout), _ptr(dQ), _ptr(dt_dev), int(stage),
                             _stream(stream)), "dg_rk_stage")
@@ -371,6 +378,28 @@ class Mesh:
         if integ is None and with_integrals:
             integ = torch.empty((nsteps, DG_NORMS_LEN), dtype=torch.float64, device=self.device)
         dg_advance(self.h, self._chk(Q), self._chk(dQ), cfl, nsteps, dts, integ, stream)
+        return dts, integ
+
+    def advance_host(self, Q_host, Q, dQ, cfl, nsteps, dts=None, integ=None, with_integrals=True,
+                     stream=None):
+        """advance() on a state held in host memory (dg_advance_host):
+        Q_host (a contiguous CPU tensor of the state, pinned for full copy
+        bandwidth) is copied to the device state Q, stepped, and copied
+        back; returns (dts, integ) as host tensors.  Synchronises."""
+        if (Q_host.dtype != self.dtype or Q_host.is_cuda or not Q_host.is_contiguous()
+                or Q_host.numel() != NF * self.n_dof):
+            raise ValueError("host state must be a contiguous CPU tensor of the mesh's "
+                             f"shape {self.shape} and dtype {self.dtype}")
+        if dts is None:
+            dts = torch.empty(nsteps, dtype=torch.float64, pin_memory=True)
+        if integ is None and with_integrals:
+            integ = torch.empty((nsteps, DG_NORMS_LEN), dtype=torch.float64, pin_memory=True)
+        for t in (dts, integ):
+            if t is not None and (t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous()):
+                raise ValueError("dts / integ must be contiguous float64 CPU tensors")
+        if dts.numel() < nsteps or (integ is not None and integ.numel() < nsteps * DG_NORMS_LEN):
+            raise ValueError("dts / integ too small for nsteps")
+        dg_advance_host(self.h, Q_host, self._chk(Q), self._chk(dQ), cfl, nsteps, dts, integ, stream)
         return dts, integ
 
     def rk_stage(self, Qin, Qout, dQ, dt, stage, stream=None):

@@ -145,3 +145,5 @@ def test_new_entry_points_reject_bad_arguments_on_host(lib):
     assert lib.dg_dmma_throughput(2, None, None) == 1
     lib.dg_selfcheck_sqrt.argtypes = [vp, vp, vp, ctypes.c_int64, vp]
     assert lib.dg_selfcheck_sqrt(None, None, None, 4, None) == 1
+    lib.dg_advance_host.argtypes = [vp, vp, vp, vp, ctypes.c_double, i, vp, vp, vp]
+    assert lib.dg_advance_host(None, None, None, None, 0.5, 1, None, None, None) == 1
