@@ -319,6 +319,9 @@ class Mesh:
         with torch.cuda.device(self.device):
             self.h = dg_mesh_create(nx, ny, nz, p, x0, y0, z0, Lx, Ly, Lz, gamma, precision)
         self.nx, self.ny, self.nz, self.p = nx, ny, nz, p
+        # the arguments that recreate this mesh (checkpoint.py)
+        self.spec = dict(nx=nx, ny=ny, nz=nz, p=p, x0=x0, y0=y0, z0=z0, Lx=Lx, Ly=Ly, Lz=Lz,
+                         gamma=gamma, precision=precision)
         self.N = p + 1
         self.E = nx * ny * nz
         self.precision = precision
