@@ -1,8 +1,9 @@
 """The workloads' own checks, through the GPU path (dg_advance, FP64):
 
 * config 1 -- isentropic vortex, [0,10]^3, 8^3 elements, p = 3, ten
-  LSERK45 steps at CFL 0.5 with seeded vortex strength, centre and drift:
-  against the oracle's ten steps (each step's time step from its own state);
+  LSERK45 steps at CFL 0.5 with seeded vortex strength, centre and drift
+  (seeds 0..9): against the oracle's ten steps (each step's time step from
+  its own state);
 * config 2 downsampled -- Taylor-Green at Mach 0.1 on 16^3 elements, p = 4,
   the config's 100 steps: state, kinetic energy and the five conserved
   integrals against the oracle's, conservation to round-off;
@@ -34,7 +35,7 @@ def _oracle_run(om, Q, cfl, nsteps):
     return Q, np.array(dts), np.array(kes)
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("seed", range(10))
 def test_config1_vortex8_p3_ten_steps(seed):
     dg = dg_module()
     import torch
