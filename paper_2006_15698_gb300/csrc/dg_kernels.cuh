@@ -198,7 +198,7 @@ __device__ __forceinline__ double trace_line(const double *l, const double *__re
 // z slabs (g.zlo set): the +z face of the last layer takes its right state
 // from the halo zhi, and layer 0's threads also evaluate their -z face
 // (left state from the halo zlo) into g.zflux, with the same code.
-template <int N, int DIR, typename real>
+template <int N, int DIR, typename real, bool HALO>
 __device__ __forceinline__ void face_point(const real *__restrict__ Q, real *__restrict__ F,
                                            const Ops<real> &T, const Geo &g, long long e, int pt)
 {
@@ -208,7 +208,7 @@ __device__ __forceinline__ void face_point(const real *__restrict__ Q, real *__r
     constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? N : N2);
     const long long plane = (long long)g.nx * g.ny;
     const long long ez = DIR == 2 ? e / plane : 0;
-    const bool slab = DIR == 2 && g.zlo != nullptr;
+    const bool slab = HALO && DIR == 2 && g.zlo != nullptr;
     const int faces = slab && ez == 0 ? 2 : 1;
 #pragma unroll 1
     for (int side = 0; side < faces; ++side) {
@@ -259,7 +259,7 @@ struct FaceTile {
     static constexpr int THREADS = 3 * SEG;
 };
 
-template <int N, typename real>
+template <int N, typename real, bool HALO>
 __global__ void __launch_bounds__(FaceTile<N>::THREADS, 1152 / FaceTile<N>::THREADS)
     face_flux_kernel(const real *__restrict__ Q, real *__restrict__ F, const Ops<real> T,
                      const Geo g)
@@ -272,9 +272,9 @@ __global__ void __launch_bounds__(FaceTile<N>::THREADS, 1152 / FaceTile<N>::THRE
     const int pt = r - el * N2;
     const long long e = (long long)blockIdx.x * EF + el;
     if (e >= g.E) return;
-    if (d == 0) face_point<N, 0>(Q, F, T, g, e, pt);
-    else if (d == 1) face_point<N, 1>(Q, F, T, g, e, pt);
-    else face_point<N, 2>(Q, F, T, g, e, pt);
+    if (d == 0) face_point<N, 0, real, HALO>(Q, F, T, g, e, pt);
+    else if (d == 1) face_point<N, 1, real, HALO>(Q, F, T, g, e, pt);
+    else face_point<N, 2, real, HALO>(Q, F, T, g, e, pt);
 }
 
 // ---------------------------------------------------------------------------
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(FaceTile<N>::THREADS, 1152 / FaceTile<N>::THRE
 
 // MODE 0: write R = dQ/dt.   MODE 1: LSERK stage, dQ <- A dQ + dt R,
 // Q <- Q + B dQ, in place (first stage: A == 0 and dQ is not read).
-template <int N, typename real, int MODE>
+template <int N, typename real, int MODE, bool HALO>
 __global__ void __launch_bounds__(Tile<N>::THREADS)
     volume_kernel(const real *Qin, real *Out, real *dQ, const real *__restrict__ F,
                   const Ops<real> T, const Geo g, real A, real B, const double *__restrict__ dt)
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
     const long long plane = (long long)g.nx * g.ny;
     const real *fzm = F + fidx(2, 0, ezm, j * N + i, g.E, N2);
     long long fzm_stride = g.E * N2;  // between fields
-    if (g.zflux != nullptr && e < plane) {
+    if (HALO && g.zflux != nullptr && e < plane) {
         fzm = static_cast<const real *>(g.zflux) + e * N2 + j * N + i;
         fzm_stride = plane * N2;
     }
@@ -943,7 +943,12 @@ cudaError_t launch_face(const Geo &g, const Ops<real> &T, const real *Q, real *F
     const long long blocks = (g.E + EF - 1) / EF;
     if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
     ProfScope ps(prof, kKindFace, s);
-    face_flux_kernel<N, real><<<(unsigned)blocks, FaceTile<N>::THREADS, 0, s>>>(Q, F, T, g);
+    // z slabs (halos set) run their own instantiation, so that the periodic
+    // kernel carries no halo code
+    if (g.zlo != nullptr)
+        face_flux_kernel<N, real, true><<<(unsigned)blocks, FaceTile<N>::THREADS, 0, s>>>(Q, F, T, g);
+    else
+        face_flux_kernel<N, real, false><<<(unsigned)blocks, FaceTile<N>::THREADS, 0, s>>>(Q, F, T, g);
     return cudaGetLastError();
 }
 
@@ -954,17 +959,18 @@ cudaError_t launch_volume(const Geo &g, const Ops<real> &T, const real *Qin, rea
 {
     constexpr int EPB = Tile<N>::EPB, THREADS = Tile<N>::THREADS, N3 = N * N * N;
     const size_t smem = ((size_t)EPB * 3 * NF * N3 + Tile<N>::OPS) * sizeof(real);
+    // z slabs (halos set) run their own instantiation, as for the face kernel
+    auto kernel = g.zflux != nullptr ? volume_kernel<N, real, MODE, true>
+                                     : volume_kernel<N, real, MODE, false>;
     if (smem > 48 * 1024) {  // opt in above the default dynamic shared-memory limit
-        cudaError_t err = cudaFuncSetAttribute(volume_kernel<N, real, MODE>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);
         if (err != cudaSuccess) return err;
     }
     const long long blocks = (g.E + EPB - 1) / EPB;
     if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
     ProfScope ps(prof, kKindVolume, s);
-    volume_kernel<N, real, MODE><<<(unsigned)blocks, THREADS, smem, s>>>(Qin, Out, dQ, F, T, g, A,
-                                                                          B, dt);
+    kernel<<<(unsigned)blocks, THREADS, smem, s>>>(Qin, Out, dQ, F, T, g, A, B, dt);
     return cudaGetLastError();
 }
 
