@@ -262,7 +262,9 @@ def fp64_peak(dg):
 
 def kernel_flops(kind, N, E):
     """Algorithmic flops per launch of the kernels (FMA = 2, div = sqrt = 1),
-    counted from the arithmetic the kernels execute per node / face point."""
+    counted from the plain formulas per node / face point (the face kernel's
+    regrouped Lax-Friedrichs components execute fewer: the count is the
+    method's work, not the instructions issued)."""
     if kind == "volume":  # flux 28 + contraction 30N + lift 60 + RK update 25, per node
         return E * N ** 3 * (113 + 30 * N)
     if kind == "face":  # traces 20N + Lax-Friedrichs 69, per unique face point
