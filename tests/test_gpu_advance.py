@@ -105,3 +105,25 @@ def test_advance_flags_nonpositive_pressure_and_rejects_bad_arguments():
     dts, _ = m.advance(to_dev(bad), dQ, 0.5, 1)
     assert math.isnan(float(dts[0].item()))
     assert m.last_error() == dg.DG_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_mesh_create_reports_oom_and_the_context_stays_usable(prec):
+    """A mesh whose workspace cannot be allocated (10^9 elements at p = 3:
+    1.3 TB of float or 1.9 TB of double workspace, beyond any one GPU) is
+    refused with DG_ERR_OOM; the failed allocation leaves nothing behind, and
+    the next mesh steps as usual (host-side failure, no device fault)."""
+    dg = dg_module()
+    import torch
+    precision = dg.DG_FP64 if prec == "fp64" else dg.DG_FP32
+    with pytest.raises(dg.DGError) as ei:
+        dg.Mesh(1000, 1000, 1000, 3, precision=precision)
+    assert ei.value.status == dg.DG_ERR_OOM
+    om = oracle.Mesh(3, 2, 2, 2, *BOX)
+    Q = _state(om, 1)
+    m = dg.Mesh(3, 2, 2, 2, *BOX, precision=precision)
+    Qd = to_dev(Q).to(m.dtype)
+    dQ = torch.zeros_like(Qd)
+    dts, integ = m.advance(Qd, dQ, 0.5, 2)
+    assert torch.isfinite(dts).all() and torch.isfinite(Qd).all()
+    assert m.last_error() == dg.DG_OK
