@@ -13,6 +13,10 @@
 
 #include "dg_internal.h"
 
+// ranges of z layers the last stage of dg_advance_host (double state) is run
+// in, each copied back to the host while the next ones compute
+constexpr int kCopyChunks = 8;
+
 struct dg_mesh {
     dg::Geo geo;
     dg_precision prec;
@@ -26,6 +30,10 @@ struct dg_mesh {
     // so far (allocated on first use)
     double *io = nullptr;
     size_t io_cap = 0;
+    // dg_advance_host, double state: the copy stream and its events (created
+    // on first use) for the copy-back overlapped with the last stage
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_ev[kCopyChunks + 1] = {};
 };
 
 namespace {
@@ -249,6 +257,9 @@ void dg_mesh_destroy(dg_mesh *m)
     cudaFree(m->work.lam_bits);
     cudaFree(m->work.err);
     cudaFree(m->io);
+    for (cudaEvent_t e : m->copy_ev)
+        if (e) cudaEventDestroy(e);
+    if (m->copy_stream) cudaStreamDestroy(m->copy_stream);
     if (m->prof) {
         for (cudaEvent_t e : m->prof->ev) cudaEventDestroy(e);
         for (cudaEvent_t e : m->prof->pool) cudaEventDestroy(e);
@@ -368,11 +379,56 @@ dg_status dg_advance_host(dg_mesh *m, void *Q_host, void *Q, void *dQ, double cf
     const size_t bytes = (size_t)dg::NF * (size_t)m->geo.E * N * N * N *
                          (m->prec == DG_FP64 ? sizeof(double) : sizeof(float));
     double *dts = m->io, *integ = integ_host ? m->io + nsteps : nullptr;
-    cudaError_t e = cudaMemcpyAsync(Q, Q_host, bytes, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaSuccess;
+    // the overlapped copy-back needs page-locked host memory (a copy into
+    // pageable memory holds the host thread until it is done, which would
+    // serialise the ranges)
+    bool overlap = false;
+    if (m->prec == DG_FP64) {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, Q_host) == cudaSuccess)
+            overlap = pa.type == cudaMemoryTypeHost;
+        else
+            cudaGetLastError();
+    }
+    if (overlap && !m->copy_stream) {
+        e = cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking);
+        for (int c = 0; c <= kCopyChunks && e == cudaSuccess; ++c)
+            e = cudaEventCreateWithFlags(&m->copy_ev[c], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            for (cudaEvent_t &ev : m->copy_ev)
+                if (ev) { cudaEventDestroy(ev); ev = nullptr; }
+            if (m->copy_stream) { cudaStreamDestroy(m->copy_stream); m->copy_stream = nullptr; }
+            return DG_ERR_CUDA;
+        }
+    }
+    e = cudaMemcpyAsync(Q, Q_host, bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_status(e);
-    const dg_status st = dg_advance(m, Q, dQ, cfl, nsteps, dts, integ, stream);
-    if (st != DG_OK) return st;
-    e = cudaMemcpyAsync(Q_host, Q, bytes, cudaMemcpyDeviceToHost, s);
+    if (overlap) {
+        // the new state goes back range by range during the last stage
+        // (kernels and floats as dg_advance; the copies on the mesh's copy
+        // stream, joined into the caller's stream before the time steps)
+        dg::CopyOut co;
+        co.host = Q_host;
+        co.stream = m->copy_stream;
+        co.ev = m->copy_ev;
+        co.chunks = kCopyChunks;
+        dg::Work w = m->work;
+        w.out = &co;
+        e = dg::Launch<double>::advance(m->geo, m->ops64, (double *)Q, (double *)dQ, cfl, nsteps,
+                                        dts, integ, w, s);
+        if (e == cudaSuccess) e = cudaEventRecord(m->copy_ev[kCopyChunks], m->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->copy_ev[kCopyChunks], 0);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(m->copy_stream);
+            return cuda_status(e);
+        }
+    } else {
+        const dg_status st = dg_advance(m, Q, dQ, cfl, nsteps, dts, integ, stream);
+        if (st != DG_OK) return st;
+        e = cudaMemcpyAsync(Q_host, Q, bytes, cudaMemcpyDeviceToHost, s);
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dts_host, dts, (size_t)nsteps * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && integ_host)

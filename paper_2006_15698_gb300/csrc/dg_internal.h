@@ -95,7 +95,19 @@ struct Prof {
 };
 
 // Device workspace owned by a mesh handle.
+// dg_advance_host's copy-back of the new state, overlapped with the last
+// step's fifth stage (double state): that stage's volume kernel runs in
+// `chunks` ranges of whole z layers, and after each range its part of every
+// field plane is copied to `host` on `stream` (which waits on ev[c]).
+struct CopyOut {
+    void *host = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t *ev = nullptr;  // one per chunk
+    int chunks = 0;
+};
+
 struct Work {
+    const CopyOut *out = nullptr;           // set by dg_advance_host only
     void *face_flux = nullptr;              // 3 * NF * E * N^2 scalars
     double *partials = nullptr;             // norms partial sums, kNormBlocks x 8
     unsigned long long *lam_bits = nullptr; // CFL maximum (bits of a positive double)

@@ -286,7 +286,8 @@ __global__ void __launch_bounds__(FaceTile<N>::THREADS, 1152 / FaceTile<N>::THRE
 template <int N, typename real, int MODE, bool HALO>
 __global__ void __launch_bounds__(Tile<N>::THREADS)
     volume_kernel(const real *Qin, real *Out, real *dQ, const real *__restrict__ F,
-                  const Ops<real> T, const Geo g, real A, real B, const double *__restrict__ dt)
+                  const Ops<real> T, const Geo g, real A, real B, const double *__restrict__ dt,
+                  long long e_begin, long long e_end)
 {
     constexpr int N2 = N * N, N3 = N * N * N, EPB = Tile<N>::EPB;
     extern __shared__ unsigned char smem_raw[];
@@ -298,8 +299,8 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
     const int tid = threadIdx.x;
     const int el = tid / N3;
     const int node = tid - el * N3;
-    const long long e = (long long)blockIdx.x * EPB + el;
-    const bool active = el < EPB && e < g.E;
+    const long long e = e_begin + (long long)blockIdx.x * EPB + el;
+    const bool active = el < EPB && e < e_end;
     const int i = node % N, j = (node / N) % N, k = node / N2;
 
     // the operators, scaled once per CTA by dt for the stage update (so the
@@ -952,11 +953,13 @@ cudaError_t launch_face(const Geo &g, const Ops<real> &T, const real *Q, real *F
     return cudaGetLastError();
 }
 
+// elements [e_begin, e_end) (the whole mesh: 0, g.E)
 template <int N, typename real, int MODE>
 cudaError_t launch_volume(const Geo &g, const Ops<real> &T, const real *Qin, real *Out, real *dQ,
                           const real *F, real A, real B, const double *dt, Prof *prof,
-                          cudaStream_t s)
+                          cudaStream_t s, long long e_begin = 0, long long e_end = -1)
 {
+    if (e_end < 0) e_end = g.E;
     constexpr int EPB = Tile<N>::EPB, THREADS = Tile<N>::THREADS, N3 = N * N * N;
     const size_t smem = ((size_t)EPB * 3 * NF * N3 + Tile<N>::OPS) * sizeof(real);
     // z slabs (halos set) run their own instantiation, as for the face kernel
@@ -967,10 +970,11 @@ cudaError_t launch_volume(const Geo &g, const Ops<real> &T, const real *Qin, rea
                                                (int)smem);
         if (err != cudaSuccess) return err;
     }
-    const long long blocks = (g.E + EPB - 1) / EPB;
+    const long long blocks = (e_end - e_begin + EPB - 1) / EPB;
+    if (blocks <= 0) return cudaSuccess;
     if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
     ProfScope ps(prof, kKindVolume, s);
-    kernel<<<(unsigned)blocks, THREADS, smem, s>>>(Qin, Out, dQ, F, T, g, A, B, dt);
+    kernel<<<(unsigned)blocks, THREADS, smem, s>>>(Qin, Out, dQ, F, T, g, A, B, dt, e_begin, e_end);
     return cudaGetLastError();
 }
 
@@ -1161,9 +1165,33 @@ cudaError_t rk_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, const doub
         for (int st = 0; st < 5; ++st) {
             cudaError_t err = launch_face<N>(g, T, Q, F, w.prof, s);
             if (err != cudaSuccess) return err;
-            err = launch_volume<N, real, 1>(g, T, Q, Q, dQ, F, real(kRkA[st]), real(kRkB[st]),
-                                            dt, w.prof, s);
-            if (err != cudaSuccess) return err;
+            if (st < 4 || w.out == nullptr) {
+                err = launch_volume<N, real, 1>(g, T, Q, Q, dQ, F, real(kRkA[st]),
+                                                real(kRkB[st]), dt, w.prof, s);
+                if (err != cudaSuccess) return err;
+                continue;
+            }
+            // the fifth stage in ranges of whole z layers, each range's part
+            // of the new state copied to the host (w.out) on the copy stream
+            // as soon as it is written, while the next ranges compute
+            const CopyOut &co = *w.out;
+            const long long plane = (long long)g.nx * g.ny, N3 = (long long)N * N * N;
+            for (int c = 0; c < co.chunks; ++c) {
+                const long long e0 = plane * ((long long)g.nz * c / co.chunks);
+                const long long e1 = plane * ((long long)g.nz * (c + 1) / co.chunks);
+                if (e1 <= e0) continue;
+                err = launch_volume<N, real, 1>(g, T, Q, Q, dQ, F, real(kRkA[st]),
+                                                real(kRkB[st]), dt, w.prof, s, e0, e1);
+                if (err == cudaSuccess) err = cudaEventRecord(co.ev[c], s);
+                if (err == cudaSuccess) err = cudaStreamWaitEvent(co.stream, co.ev[c], 0);
+                for (int n = 0; n < NF && err == cudaSuccess; ++n) {
+                    const long long off = ((long long)n * g.E + e0) * N3;
+                    err = cudaMemcpyAsync(static_cast<real *>(co.host) + off, Q + off,
+                                          (size_t)((e1 - e0) * N3) * sizeof(real),
+                                          cudaMemcpyDeviceToHost, co.stream);
+                }
+                if (err != cudaSuccess) return err;
+            }
         }
         return cudaSuccess;
     }
@@ -1371,7 +1399,11 @@ cudaError_t advance_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, doubl
         // slower than the two passes, which it would only save one read of
         // the state
         for (int k = 0; k < nsteps; ++k) {
-            err = rk_n<N, real>(g, T, Q, dQ, dts + k, w, s);
+            // the copy-back of the new state (dg_advance_host) overlaps the
+            // last step's fifth stage only
+            Work wk = w;
+            if (k + 1 < nsteps) wk.out = nullptr;
+            err = rk_n<N, real>(g, T, Q, dQ, dts + k, wk, s);
             if (err != cudaSuccess) return err;
             if (norms) {
                 err = Launch<real>::norms(g, Q, nullptr, integ + (size_t)k * DG_NORMS_LEN, w, s);

@@ -1,8 +1,10 @@
 """dg_advance_host: the state in host memory, copied in, stepped and copied
 back by one library call, equals dg_advance on the device copy bit for bit
 (state, time steps, integrals), for both precisions and odd and even step
-counts, with pinned and pageable host buffers; bad arguments are refused
-before any copy."""
+counts, with pinned and pageable host buffers (the double form's pinned
+copy-back runs during the last stage, in ranges of z layers: meshes with
+fewer layers than ranges, a ragged split and an even one); bad arguments
+are refused before any copy."""
 import pytest
 
 import oracle
@@ -15,7 +17,8 @@ BOX = (0.0, 0.0, 0.0, 10.0, 10.0, 10.0)
 
 
 @pytest.mark.parametrize("prec,p,nel", [("fp64", 3, (4, 3, 5)), ("fp32", 3, (5, 4, 3)),
-                                        ("fp32", 4, (3, 3, 2)), ("fp64", 1, (2, 5, 3))])
+                                        ("fp32", 4, (3, 3, 2)), ("fp64", 1, (2, 5, 3)),
+                                        ("fp64", 2, (3, 2, 11)), ("fp64", 4, (2, 2, 16))])
 @pytest.mark.parametrize("nsteps", [1, 2, 3])
 def test_host_call_equals_device_call(prec, p, nel, nsteps):
     dg = dg_module()
