@@ -245,11 +245,12 @@ dg_status dg_advance(const dg_mesh *mesh, void *Q, void *dQ, double cfl, int nst
  * integ_host.  The call returns once `stream` has finished all of it
  * (synchronises).  Host buffers should be page-locked (cudaHostAlloc, a
  * pinned torch tensor): pageable memory works but is staged by the driver.
- * DG_FP64 with a page-locked Q_host: the last step's fifth stage runs in 8
- * ranges of whole z layers and each range of the new state is copied back
- * while the next ranges and the integrals compute, on a stream and events the
- * mesh creates on the first such call (the same kernels and floats as
- * dg_advance).  The time steps and integrals pass through a device buffer
+ * DG_FP64 with a page-locked Q_host: the state moves in 8 ranges of whole z
+ * layers on a stream and events the mesh creates on the first such call: in,
+ * with the first time-step reduction and the first stage's face kernel
+ * following each range as it lands; back, each range of the new state while
+ * the last stage computes the next ranges and the integrals (the same
+ * kernels and floats as dg_advance).  The time steps and integrals pass through a device buffer
  * the mesh keeps for the largest nsteps so far (the first call, or a larger nsteps,
  * allocates it: not for code that cannot allocate).  Errors: those of
  * dg_advance (checked before any copy), DG_ERR_OOM, DG_ERR_CUDA. */

@@ -13,8 +13,9 @@
 
 #include "dg_internal.h"
 
-// ranges of z layers the last stage of dg_advance_host (double state) is run
-// in, each copied back to the host while the next ones compute
+// ranges of z layers in which dg_advance_host (double state) moves the state:
+// in, each range followed by the first reduction and face kernel over it;
+// back, each range copied while the last stage computes the next ones
 constexpr int kCopyChunks = 8;
 
 struct dg_mesh {
@@ -31,9 +32,11 @@ struct dg_mesh {
     double *io = nullptr;
     size_t io_cap = 0;
     // dg_advance_host, double state: the copy stream and its events (created
-    // on first use) for the copy-back overlapped with the last stage
+    // on first use) for the copy-in overlapped with the first reduction and
+    // face kernel, and the copy-back overlapped with the last stage
+    // (copy-back: ranges 0..K-1 and the end; copy-in: K+1 .. 2K+1)
     cudaStream_t copy_stream = nullptr;
-    cudaEvent_t copy_ev[kCopyChunks + 1] = {};
+    cudaEvent_t copy_ev[2 * kCopyChunks + 2] = {};
 };
 
 namespace {
@@ -393,7 +396,7 @@ dg_status dg_advance_host(dg_mesh *m, void *Q_host, void *Q, void *dQ, double cf
     }
     if (overlap && !m->copy_stream) {
         e = cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking);
-        for (int c = 0; c <= kCopyChunks && e == cudaSuccess; ++c)
+        for (int c = 0; c < 2 * kCopyChunks + 2 && e == cudaSuccess; ++c)
             e = cudaEventCreateWithFlags(&m->copy_ev[c], cudaEventDisableTiming);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -403,18 +406,27 @@ dg_status dg_advance_host(dg_mesh *m, void *Q_host, void *Q, void *dQ, double cf
             return DG_ERR_CUDA;
         }
     }
-    e = cudaMemcpyAsync(Q, Q_host, bytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (!overlap) {
+        e = cudaMemcpyAsync(Q, Q_host, bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
     if (overlap) {
-        // the new state goes back range by range during the last stage
-        // (kernels and floats as dg_advance; the copies on the mesh's copy
-        // stream, joined into the caller's stream before the time steps)
+        // the state comes in range by range, the first reduction and face
+        // kernel following it, and goes back range by range during the last
+        // stage (kernels and floats as dg_advance; the copies on the mesh's
+        // copy stream, joined into the caller's stream before the time steps)
+        dg::CopyIn ci;
+        ci.host = Q_host;
+        ci.stream = m->copy_stream;
+        ci.ev = m->copy_ev + kCopyChunks + 1;
+        ci.chunks = kCopyChunks;
         dg::CopyOut co;
         co.host = Q_host;
         co.stream = m->copy_stream;
         co.ev = m->copy_ev;
         co.chunks = kCopyChunks;
         dg::Work w = m->work;
+        w.in = &ci;
         w.out = &co;
         e = dg::Launch<double>::advance(m->geo, m->ops64, (double *)Q, (double *)dQ, cfl, nsteps,
                                         dts, integ, w, s);

@@ -106,8 +106,21 @@ struct CopyOut {
     int chunks = 0;
 };
 
+// dg_advance_host's copy-in of the state (double state): the state arrives
+// on `stream` in `chunks` ranges of whole z layers (ev[c] recorded after
+// range c; ev[chunks] marks the start), and the first time-step reduction and
+// the first stage's face kernel follow it range by range.
+struct CopyIn {
+    const void *host = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t *ev = nullptr;  // chunks + 1
+    int chunks = 0;
+};
+
 struct Work {
     const CopyOut *out = nullptr;           // set by dg_advance_host only
+    const CopyIn *in = nullptr;             // set by dg_advance_host only
+    bool first_face_done = false;           // the step's first face kernel already ran
     void *face_flux = nullptr;              // 3 * NF * E * N^2 scalars
     double *partials = nullptr;             // norms partial sums, kNormBlocks x 8
     unsigned long long *lam_bits = nullptr; // CFL maximum (bits of a positive double)

@@ -262,7 +262,7 @@ struct FaceTile {
 template <int N, typename real, bool HALO>
 __global__ void __launch_bounds__(FaceTile<N>::THREADS, 1152 / FaceTile<N>::THREADS)
     face_flux_kernel(const real *__restrict__ Q, real *__restrict__ F, const Ops<real> T,
-                     const Geo g)
+                     const Geo g, long long e_begin, long long e_end)
 {
     constexpr int N2 = N * N, EF = FaceTile<N>::EF, SEG = FaceTile<N>::SEG;
     const int d = threadIdx.x / SEG;
@@ -270,8 +270,8 @@ __global__ void __launch_bounds__(FaceTile<N>::THREADS, 1152 / FaceTile<N>::THRE
     if (r >= EF * N2) return;
     const int el = r / N2;
     const int pt = r - el * N2;
-    const long long e = (long long)blockIdx.x * EF + el;
-    if (e >= g.E) return;
+    const long long e = e_begin + (long long)blockIdx.x * EF + el;
+    if (e >= e_end) return;
     if (d == 0) face_point<N, 0, real, HALO>(Q, F, T, g, e, pt);
     else if (d == 1) face_point<N, 1, real, HALO>(Q, F, T, g, e, pt);
     else face_point<N, 2, real, HALO>(Q, F, T, g, e, pt);
@@ -543,9 +543,11 @@ __device__ __forceinline__ void block_lambda(double m, bool bad, unsigned long l
 // Double state: the float pre-filter above; float state: node speeds in float.
 template <typename real>
 __global__ void __launch_bounds__(256) cfl_kernel(const real *__restrict__ Q, long long nodes,
+                                                  long long t_begin, long long t_end,
                                                   double gamma, unsigned long long *lam_bits,
                                                   int *err)
 {
+    // nodes t_begin .. t_end - 1 of every field (field stride: nodes)
     double m = 0.0;
     bool bad = false;
     if constexpr (std::is_same<real, double>::value) {
@@ -553,10 +555,10 @@ __global__ void __launch_bounds__(256) cfl_kernel(const real *__restrict__ Q, lo
         const long long stride = (long long)gridDim.x * blockDim.x;  // a multiple of 32
         float R = 0.0f;
         // whole warps walk the nodes together, so the shuffles stay convergent
-        for (long long tb = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); tb < nodes;
-             tb += stride) {
+        for (long long tb = t_begin + (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+             tb < t_end; tb += stride) {
             const long long t = tb + lane;
-            const bool in = t < nodes;
+            const bool in = t < t_end;
             double r = 1.0, mx = 0.0, my = 0.0, mz = 0.0, E = 0.0;
             if (in) {
                 r = Q[t]; mx = Q[nodes + t]; my = Q[2 * nodes + t]; mz = Q[3 * nodes + t];
@@ -567,7 +569,7 @@ __global__ void __launch_bounds__(256) cfl_kernel(const real *__restrict__ Q, lo
     } else {
         const float gf = (float)gamma;
         float mf = 0.0f;
-        for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nodes;
+        for (long long t = t_begin + (long long)blockIdx.x * blockDim.x + threadIdx.x; t < t_end;
              t += (long long)gridDim.x * blockDim.x) {
             float sp;
             if (!node_speed_f(Q[t], Q[nodes + t], Q[2 * nodes + t], Q[3 * nodes + t],
@@ -936,20 +938,25 @@ struct ProfScope {
 
 constexpr long long kMaxGridX = 2147483647LL;
 
+// the +faces of elements [e_begin, e_end) (the whole mesh: 0, g.E)
 template <int N, typename real>
 cudaError_t launch_face(const Geo &g, const Ops<real> &T, const real *Q, real *F, Prof *prof,
-                        cudaStream_t s)
+                        cudaStream_t s, long long e_begin = 0, long long e_end = -1)
 {
     constexpr int EF = FaceTile<N>::EF;
-    const long long blocks = (g.E + EF - 1) / EF;
+    if (e_end < 0) e_end = g.E;
+    const long long blocks = (e_end - e_begin + EF - 1) / EF;
+    if (blocks <= 0) return cudaSuccess;
     if (blocks > kMaxGridX) return cudaErrorInvalidConfiguration;
     ProfScope ps(prof, kKindFace, s);
     // z slabs (halos set) run their own instantiation, so that the periodic
     // kernel carries no halo code
     if (g.zlo != nullptr)
-        face_flux_kernel<N, real, true><<<(unsigned)blocks, FaceTile<N>::THREADS, 0, s>>>(Q, F, T, g);
+        face_flux_kernel<N, real, true><<<(unsigned)blocks, FaceTile<N>::THREADS, 0, s>>>(
+            Q, F, T, g, e_begin, e_end);
     else
-        face_flux_kernel<N, real, false><<<(unsigned)blocks, FaceTile<N>::THREADS, 0, s>>>(Q, F, T, g);
+        face_flux_kernel<N, real, false><<<(unsigned)blocks, FaceTile<N>::THREADS, 0, s>>>(
+            Q, F, T, g, e_begin, e_end);
     return cudaGetLastError();
 }
 
@@ -1163,7 +1170,8 @@ cudaError_t rk_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, const doub
     } else {
         real *F = static_cast<real *>(w.face_flux);
         for (int st = 0; st < 5; ++st) {
-            cudaError_t err = launch_face<N>(g, T, Q, F, w.prof, s);
+            cudaError_t err = cudaSuccess;
+            if (st > 0 || !w.first_face_done) err = launch_face<N>(g, T, Q, F, w.prof, s);
             if (err != cudaSuccess) return err;
             if (st < 4 || w.out == nullptr) {
                 err = launch_volume<N, real, 1>(g, T, Q, Q, dQ, F, real(kRkA[st]),
@@ -1352,8 +1360,8 @@ cudaError_t Launch<real>::cfl(const Geo &g, const real *Q, double cfl, double *d
     const int N = g.p + 1;
     const long long nodes = g.E * N * N * N;
     ProfScope ps(w.prof, kKindCfl, s);
-    cfl_kernel<real><<<grid_for(nodes, 256, 8LL * sm_count()), 256, 0, s>>>(Q, nodes, g.gamma, w.lam_bits,
-                                                                    w.err);
+    cfl_kernel<real><<<grid_for(nodes, 256, 8LL * sm_count()), 256, 0, s>>>(
+        Q, nodes, 0, nodes, g.gamma, w.lam_bits, w.err);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     cfl_finalize_kernel<<<1, 1, 0, s>>>(w.lam_bits, cfl, g.hmin, g.p, dt);
@@ -1386,11 +1394,73 @@ cudaError_t Launch<real>::init(const Geo &g, int kind, const double *params, rea
     return cudaGetLastError();
 }
 
+// dg_advance_host's copy-in (double state): the host state arrives in ranges
+// of whole z layers on the copy stream; the first time-step reduction runs
+// over each range as it lands, and the first stage's face kernel over the
+// elements of range c once range c + 1 (their +z neighbours) has landed too
+// (the last range's neighbours are range 0).  The reduction's maximum is exact,
+// so its partition does not change the time step.
+template <int N, typename real>
+cudaError_t copy_in_prologue(const Geo &g, const Ops<real> &T, real *Q, double cfl, double *dt,
+                             Work &w, cudaStream_t s)
+{
+    const CopyIn &ci = *w.in;
+    const long long plane = (long long)g.nx * g.ny, N3 = (long long)N * N * N;
+    const long long nodes = g.E * N3;
+    const int K = ci.chunks;
+    auto lo = [&](int c) { return plane * ((long long)g.nz * c / K); };
+    // the copy stream starts once the caller's earlier work on s is done
+    cudaError_t err = cudaEventRecord(ci.ev[K], s);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(ci.stream, ci.ev[K], 0);
+    for (int c = 0; c < K && err == cudaSuccess; ++c) {
+        const long long e0 = lo(c), e1 = lo(c + 1);
+        for (int n = 0; n < NF && err == cudaSuccess && e1 > e0; ++n) {
+            const long long off = ((long long)n * g.E + e0) * N3;
+            err = cudaMemcpyAsync(Q + off, static_cast<const real *>(ci.host) + off,
+                                  (size_t)((e1 - e0) * N3) * sizeof(real), cudaMemcpyHostToDevice,
+                                  ci.stream);
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(ci.ev[c], ci.stream);
+    }
+    if (err != cudaSuccess) return err;
+    real *F = static_cast<real *>(w.face_flux);
+    int pending = -1;  // a range whose face kernel waits for the next range
+    for (int c = 0; c < K; ++c) {
+        const long long e0 = lo(c), e1 = lo(c + 1);
+        if (e1 <= e0) continue;
+        err = cudaStreamWaitEvent(s, ci.ev[c], 0);
+        if (err != cudaSuccess) return err;
+        {
+            ProfScope ps(w.prof, kKindCfl, s);
+            cfl_kernel<real><<<grid_for((e1 - e0) * N3, 256, 8LL * sm_count()), 256, 0, s>>>(
+                Q, nodes, e0 * N3, e1 * N3, g.gamma, w.lam_bits, w.err);
+            err = cudaGetLastError();
+        }
+        if (err == cudaSuccess && pending >= 0)
+            err = launch_face<N>(g, T, Q, F, w.prof, s, lo(pending), lo(pending + 1));
+        if (err != cudaSuccess) return err;
+        pending = c;
+    }
+    // the last range's +z neighbours are layer 0, landed first
+    if (pending >= 0) {
+        err = launch_face<N>(g, T, Q, F, w.prof, s, lo(pending), lo(pending + 1));
+        if (err != cudaSuccess) return err;
+    }
+    cfl_finalize_kernel<<<1, 1, 0, s>>>(w.lam_bits, cfl, g.hmin, g.p, dt);
+    return cudaGetLastError();
+}
+
 template <int N, typename real>
 cudaError_t advance_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, double cfl, int nsteps,
                       double *dts, double *integ, Work &w, cudaStream_t s)
 {
-    cudaError_t err = Launch<real>::cfl(g, Q, cfl, dts, w, s);
+    cudaError_t err = cudaSuccess;
+    if constexpr (!std::is_same<real, float>::value) {
+        if (w.in) err = copy_in_prologue<N, real>(g, T, Q, cfl, dts, w, s);
+        else err = Launch<real>::cfl(g, Q, cfl, dts, w, s);
+    } else {
+        err = Launch<real>::cfl(g, Q, cfl, dts, w, s);
+    }
     if (err != cudaSuccess) return err;
     const bool norms = integ != nullptr;
     if constexpr (!std::is_same<real, float>::value) {
@@ -1403,6 +1473,7 @@ cudaError_t advance_n(const Geo &g, const Ops<real> &T, real *Q, real *dQ, doubl
             // last step's fifth stage only
             Work wk = w;
             if (k + 1 < nsteps) wk.out = nullptr;
+            wk.first_face_done = k == 0 && w.in != nullptr;
             err = rk_n<N, real>(g, T, Q, dQ, dts + k, wk, s);
             if (err != cudaSuccess) return err;
             if (norms) {

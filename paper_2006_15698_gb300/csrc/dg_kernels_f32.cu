@@ -17,8 +17,8 @@ cudaError_t float_lambda(const Geo &g, const float *Q, unsigned long long *lam_b
                          cudaStream_t s)
 {
     const long long nodes = g.E * (long long)(g.p + 1) * (g.p + 1) * (g.p + 1);
-    cfl_kernel<float><<<grid_for(nodes, 256, 8LL * sm_count()), 256, 0, s>>>(Q, nodes, g.gamma, lam_bits,
-                                                                     err);
+    cfl_kernel<float><<<grid_for(nodes, 256, 8LL * sm_count()), 256, 0, s>>>(
+        Q, nodes, 0, nodes, g.gamma, lam_bits, err);
     return cudaGetLastError();
 }
 
