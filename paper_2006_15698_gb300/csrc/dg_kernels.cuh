@@ -105,23 +105,25 @@ __device__ __forceinline__ float recip(float x) { return 1.0f / x; }
 // sqrt(a) for the positive, finite, normal a = gamma p / rho of the sound
 // speed, on the FP64 pipe with fewer instructions than the correctly rounded
 // square root: the hardware reciprocal-square-root approximation y ~ a^-1/2
-// (rsqrt.approx.ftz.f64), one Newton-Raphson step y <- y + y (1 - a y^2)/2
-// (squares the relative error), then the root c = a y and one correction
-// c <- c + (y/2)(a - c^2) with the residual a - c^2 formed exactly by an FMA
-// (P. Markstein, "IA-64 and Elementary Functions", Prentice Hall 2000, the
-// coupled root / reciprocal-root iteration).  The result is within one ulp of
-// the correctly rounded root (checked against CUDA's sqrt on a sweep of
-// inputs, dg_selfcheck_sqrt).  a = 0 gives NaN (a zero pressure, which the
-// time-step reduction reports as non-physical).
+// (rsqrt.approx.ftz.f64) starts the coupled iteration for g ~ sqrt(a) and
+// h ~ 1/(2 sqrt(a)) (Goldschmidt's square-root iteration, as in P. Markstein,
+// "IA-64 and Elementary Functions", Prentice Hall 2000): g = a y, h = y/2,
+// r = 1/2 - g h, g <- g + g r, h <- h + h r (each squares the relative
+// error), then one correction g <- g + h (a - g^2) with the residual formed
+// exactly by an FMA.  The result is within one ulp of the correctly rounded
+// root (checked against CUDA's sqrt on a sweep of inputs, dg_selfcheck_sqrt).
+// a = 0 gives NaN (a zero pressure, which the time-step reduction reports as
+// non-physical).
 __device__ __forceinline__ double sqrt_pos(double a)
 {
     double y;
     asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
-    const double e = fma(-0.5 * a, y * y, 0.5);
-    y = fma(y, e, y);
-    const double c = a * y;
-    const double r = fma(-c, c, a);
-    return fma(r, 0.5 * y, c);
+    double g = a * y, h = 0.5 * y;
+    const double r = fma(-g, h, 0.5);
+    g = fma(g, r, g);
+    h = fma(h, r, h);
+    const double d = fma(-g, g, a);
+    return fma(d, h, g);
 }
 
 // Local Lax-Friedrichs (Rusanov) flux through a face with normal +e_DIR,
