@@ -37,7 +37,8 @@
 // many copies per thread).  PFN: the neighbour columns' elements of the next
 // layer prefetched into L2.  PL1: the current layer's neighbour-column
 // elements prefetched into L1 before the node fluxes (measured on GB300: 2 %
-// faster at p = 2, 0.5-5 % slower at p = 1 and 3..6).  RPAD: floats of padding
+// faster at p = 2, 0.5-5 % slower at p = 1 and 3..6; PFN on top of it at
+// p = 2: 1.6 % slower).  RPAD: floats of padding
 // after every element row of a slot, so that the rows of one x-interface
 // task batch fall into different banks (where a row is a multiple of 32
 // floats).
